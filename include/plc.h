@@ -1,0 +1,160 @@
+/*
+ * plc.h -- C ABI of libplc, the GB300 (sm_103a) Poisson-lognormal MAP solver.
+ *
+ * The library finds the maximum a posteriori log-density s = ln(1 + delta) on a
+ * periodic cubic grid of n^3 cells, given galaxy counts N, a completeness w,
+ * the mean count nbar, a constant prior mean mu and a tabulated power spectrum
+ * P(k) (Kitaura, Jasche & Metcalf, "Recovering the nonlinear density field
+ * from the galaxy distribution with a Poisson-Lognormal filter"):
+ *
+ *   -ln P(s|N) = 1/2 (s - mu)^T S^-1 (s - mu) + sum_i [ w_i nbar e^{s_i} - N_i s_i ]
+ *
+ * (lognormal prior of Sec. 2.3 times the Poisson likelihood of Sec. 2.1, unity
+ * bias, constants dropped), whose stationarity condition is Eq. (MAPLNUB).
+ *
+ * Conventions shared by every call
+ *   - Fields are caller-owned DEVICE pointers, C order [z][y][x] (x fastest),
+ *     n^3 elements, 16-byte aligned.  Counts N are int32.  The element type
+ *     of a field argument is stated per call: "real" means double for a
+ *     context created with PLC_FP64 and float for PLC_MIXED.
+ *   - w may be NULL, meaning w = 1 everywhere.
+ *   - The prior: S is a convolution, diagonal under the unnormalised forward
+ *     DFT (Sec. 2.2) with eigenvalue lambda_k = P(|k|) n^3 / L^3,
+ *     |k| = (2 pi / L) |m|, m in [-n/2, n/2) per axis; P is interpolated
+ *     linearly in (ln k, ln P) between table points.  The DC mode carries an
+ *     explicit inverse eigenvalue (0 = flat prior on the mean).
+ *   - Work is enqueued on the context's stream.  Calls that return host
+ *     scalars synchronise that stream before returning.
+ *   - No call throws.  Invalid arguments return PLC_ERR_INVALID_ARG with
+ *     nothing launched; plc_last_error() describes the last failure.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - The library allocates device scratch only in plc_create/plc_set_prior
+ *     and on the first use of a call that needs solver work fields.
+ */
+#ifndef PLC_H
+#define PLC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PLC_OK = 0,
+  PLC_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, bad table, no prior set */
+  PLC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  PLC_ERR_NOT_CONVERGED = 3, /* iteration cap reached; outputs hold the last iterate */
+  PLC_ERR_NONFINITE = 4,     /* NaN or Inf in the objective or gradient */
+  PLC_ERR_CG_BREAKDOWN = 5,  /* p^T H p <= 0 on the first CG step */
+  PLC_ERR_OOM = 6            /* device allocation failed */
+} plc_status;
+
+typedef enum {
+  PLC_FP64 = 0,  /* every field and FFT in double */
+  PLC_MIXED = 1  /* FP32 FFTs and pointwise work, FP64 reductions and scalars;
+                    the Newton solve keeps an FP64 master copy of s and takes
+                    its stopping gradient in FP64 */
+} plc_precision;
+
+typedef struct plc_ctx plc_ctx;
+
+/* Create a context for an n^3 grid in a periodic box of side `box` (Mpc/h).
+ * n must be even, 4 <= n <= 512, with no prime factor other than 2 and 3.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Allocates the FFT scratch (two half-spectra of the widest type). */
+plc_status plc_create(plc_ctx** ctx, int n, double box, int precision,
+                      void* cuda_stream);
+
+/* Destroy a context and free its device memory.  NULL is accepted. */
+plc_status plc_destroy(plc_ctx* ctx);
+
+/* Set the prior (Sec. 2.2-2.3): host arrays k[nk] (h/Mpc, strictly
+ * ascending, > 0) and P[nk] ((Mpc/h)^3, > 0), nk >= 2, covering every
+ * non-zero mode of the grid: k[0] <= 2 pi / L and k[nk-1] >= sqrt(3) pi n / L.
+ * mu is the constant prior mean (Sec. 2.3, Eq. mu); inv_lambda_dc the inverse
+ * eigenvalue of the DC mode (>= 0; 0 = flat prior on the mean).  The table is
+ * copied; the per-mode inverse eigenvalues are built on the device. */
+plc_status plc_set_prior(plc_ctx* ctx, const double* k, const double* P,
+                         int nk, double mu, double inv_lambda_dc);
+
+/* y = S^-1 x (Sec. 2.2): forward 3D real FFT, division by lambda_k,
+ * inverse FFT.  x, y: real fields (may alias). */
+plc_status plc_prior_apply(plc_ctx* ctx, const void* x, void* y);
+
+/* Negative log posterior and its gradient at s (Sec. 3.1.2):
+ *   g = S^-1 (s - mu) + nbar w e^s - N.
+ * s, w, grad: real fields; N: int32 field.  *neg_logpost (host, FP64,
+ * reduced in FP64) receives -ln P(s|N) without its s-independent
+ * constants.  Either output may be NULL.  Synchronises the stream when
+ * neg_logpost is not NULL. */
+plc_status plc_logpost_grad(plc_ctx* ctx, const void* s, const int32_t* N,
+                            const void* w, double nbar, double* neg_logpost,
+                            void* grad);
+
+/* Hessian-vector product at s (Sec. 3.1.2):
+ *   Hv = S^-1 v + nbar w e^s v.
+ * s, w, v, Hv: real fields (Hv may alias v). */
+plc_status plc_hessvec(plc_ctx* ctx, const void* s, const void* w,
+                       double nbar, const void* v, void* Hv);
+
+typedef struct {
+  double tol;          /* stop when ||g|| / ||g0|| < tol (default 1e-6) */
+  int max_newton;      /* outer iteration cap (default 200) */
+  int max_cg;          /* CG iterations per Newton step (default 1000) */
+  int precond;         /* 0 none, 1 Jacobi diag(H) (default 1) */
+  double g0_norm;      /* > 0: use as ||g0|| (resume); 0: ||g(s_in)|| */
+  double step_cap;     /* max |tau xi| per Newton step (default 2) */
+  double eta_max;      /* CG forcing term cap (default 0.5) */
+  int cg_chunk;        /* CG iterations enqueued between host checks (default 8) */
+} plc_opts;
+
+typedef struct {
+  int newton_iters;    /* outer iterations taken */
+  int cg_iters;        /* total CG iterations */
+  int hv_count;        /* Hessian-vector products applied */
+  int grad_evals;      /* gradient evaluations (FP64 in both modes) */
+  double grad_rel;     /* final ||g|| / ||g0|| */
+  double g0_norm;      /* ||g0|| used */
+  double neg_logpost;  /* final -ln P(s|N) (constants dropped) */
+  double ms;           /* wall time of the call, milliseconds */
+} plc_stats;
+
+/* Fill *opts with the defaults above. */
+plc_status plc_default_opts(plc_opts* opts);
+
+/* MAP by inexact Newton-Krylov (Sec. 3.1): s <- s + tau xi with tau from
+ * Eq. (New5), xi from preconditioned CG on H xi = -g, a step cap and an
+ * Armijo backtracking line search.  s_inout (double, device) holds the start
+ * point on entry (e.g. filled with mu) and the MAP on exit.  N: int32 field;
+ * w: double field or NULL (double in both precisions).  opts NULL = defaults;
+ * stats may be NULL.  Returns PLC_ERR_NOT_CONVERGED with s_inout holding the
+ * last iterate when max_newton is reached.  Synchronises the stream. */
+plc_status plc_newton_krylov_map(plc_ctx* ctx, const int32_t* N, const void* w,
+                                 double nbar, double* s_inout,
+                                 const plc_opts* opts, plc_stats* stats);
+
+/* Implicit adjoint of the MAP (implicit-function theorem on g(s*) = 0; the
+ * paper has no counterpart).  For a cotangent u (double field), solves
+ * H lam = u by CG at s_map and returns
+ *   vjp_N   = lam                               (d s* / d N is H^-1)
+ *   vjp_lnA = lam^T S^-1_{k != 0} (s_map - mu)  (d s* / d ln A, A scaling
+ *                                                every non-DC lambda_k).
+ * s_map, u, vjp_N: double fields; w: double field or NULL.  The CG stops at
+ * relative residual opts->tol (MIXED: FP32 CG, so about 1e-6 at best).
+ * Synchronises the stream. */
+plc_status plc_map_vjp(plc_ctx* ctx, const double* s_map, const void* w,
+                       double nbar, const double* u, double* vjp_N,
+                       double* vjp_lnA, const plc_opts* opts, plc_stats* stats);
+
+/* Message of the last failure on this context ("" if none). */
+const char* plc_last_error(const plc_ctx* ctx);
+
+/* Static name of a status code. */
+const char* plc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLC_H */

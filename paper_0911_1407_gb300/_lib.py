@@ -1,0 +1,220 @@
+"""ctypes binding of libplc (include/plc.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Field arguments are contiguous CUDA tensors of shape (n, n, n) in [z][y][x]
+order; PyTorch supplies device memory and the stream.  There is no CPU
+fallback: if libplc.so is missing or cannot be loaded, `load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libplc.so")
+
+PLC_FP64, PLC_MIXED = 0, 1
+STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_NOT_CONVERGED",
+          4: "PLC_ERR_NONFINITE", 5: "PLC_ERR_CG_BREAKDOWN", 6: "PLC_ERR_OOM"}
+
+# Every symbol include/plc.h declares.
+EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
+           "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
+           "plc_last_error", "plc_status_string"]
+
+
+class PlcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_cg", ctypes.c_int),
+                ("precond", ctypes.c_int), ("g0_norm", ctypes.c_double),
+                ("step_cap", ctypes.c_double), ("eta_max", ctypes.c_double),
+                ("cg_chunk", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("hv_count", ctypes.c_int), ("grad_evals", ctypes.c_int),
+                ("grad_rel", ctypes.c_double), ("g0_norm", ctypes.c_double),
+                ("neg_logpost", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libplc.so and declare its signatures (raises if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libplc.so not built at {path}; run python -m paper_0911_1407_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "plc_create": (I, [ctypes.POINTER(P), I, D, I, P]),
+        "plc_destroy": (I, [P]),
+        "plc_set_prior": (I, [P, DP, DP, I, D, D]),
+        "plc_prior_apply": (I, [P, P, P]),
+        "plc_logpost_grad": (I, [P, P, P, P, D, DP, P]),
+        "plc_hessvec": (I, [P, P, P, D, P, P]),
+        "plc_default_opts": (I, [ctypes.POINTER(Opts)]),
+        "plc_newton_krylov_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_last_error": (ctypes.c_char_p, [P]),
+        "plc_status_string": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _LIB = lib
+    return lib
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().plc_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t: Optional[torch.Tensor], n: int, dtype, name: str, required: bool = True):
+    if t is None:
+        if required:
+            raise ValueError(f"{name} is required")
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != (n, n, n) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous ({n}, {n}, {n}) tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class MapResult:
+    s: torch.Tensor
+    status: int
+    stats: dict
+
+
+class Context:
+    """One libplc context: a grid, a precision, a prior, on one CUDA stream."""
+
+    def __init__(self, n: int, box: float, precision: str = "fp64",
+                 stream: Optional[torch.cuda.Stream] = None):
+        self.lib = load()
+        self.n, self.box = int(n), float(box)
+        self.precision = {"fp64": PLC_FP64, "mixed": PLC_MIXED}[precision]
+        self.real = torch.float64 if self.precision == PLC_FP64 else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        st = self.lib.plc_create(ctypes.byref(self._h), self.n, self.box, self.precision,
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise PlcError(st, self.lib.plc_last_error(None).decode())
+        self.mu = None
+
+    # -- plumbing ----------------------------------------------------------
+    def _check(self, st: int, allow=(0,)) -> int:
+        if st not in allow:
+            raise PlcError(st, self.lib.plc_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        if self._h:
+            self.lib.plc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def field(self, dtype=None) -> torch.Tensor:
+        return torch.empty((self.n,) * 3, dtype=dtype or self.real, device="cuda")
+
+    # -- calls ---------------------------------------------------------------
+    def set_prior(self, k, P, mu: float, inv_lambda_dc: float = 0.0):
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        DP = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.plc_set_prior(self._h, k.ctypes.data_as(DP), P.ctypes.data_as(DP),
+                                           int(k.size), float(mu), float(inv_lambda_dc)))
+        self.mu = float(mu)
+
+    def prior_apply(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = self.field() if out is None else out
+        self._check(self.lib.plc_prior_apply(self._h, _ptr(x, self.n, self.real, "x"),
+                                             _ptr(out, self.n, self.real, "out")))
+        return out
+
+    def logpost_grad(self, s, N, w, nbar: float, grad: Optional[torch.Tensor] = None,
+                     want_grad: bool = True):
+        if want_grad and grad is None:
+            grad = self.field()
+        f = ctypes.c_double()
+        self._check(self.lib.plc_logpost_grad(
+            self._h, _ptr(s, self.n, self.real, "s"), _ptr(N, self.n, torch.int32, "N"),
+            _ptr(w, self.n, self.real, "w", False), float(nbar), ctypes.byref(f),
+            _ptr(grad, self.n, self.real, "grad", False)))
+        return f.value, grad
+
+    def hessvec(self, s, w, nbar: float, v, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = self.field() if out is None else out
+        self._check(self.lib.plc_hessvec(
+            self._h, _ptr(s, self.n, self.real, "s"), _ptr(w, self.n, self.real, "w", False),
+            float(nbar), _ptr(v, self.n, self.real, "v"), _ptr(out, self.n, self.real, "Hv")))
+        return out
+
+    def newton_krylov_map(self, N, w, nbar: float, s: Optional[torch.Tensor] = None,
+                          raise_on_fail: bool = True, **opts) -> MapResult:
+        """MAP; s (float64) is the start point and is overwritten (default mu)."""
+        if s is None:
+            if self.mu is None:
+                raise RuntimeError("set_prior first")
+            s = torch.full((self.n,) * 3, self.mu, dtype=torch.float64, device="cuda")
+        o, stt = default_opts(**opts), Stats()
+        st = self.lib.plc_newton_krylov_map(
+            self._h, _ptr(N, self.n, torch.int32, "N"), _ptr(w, self.n, torch.float64, "w", False),
+            float(nbar), _ptr(s, self.n, torch.float64, "s"), ctypes.byref(o), ctypes.byref(stt))
+        if raise_on_fail:
+            self._check(st)
+        return MapResult(s, st, stt.as_dict())
+
+    def map_vjp(self, s_map, w, nbar: float, u, raise_on_fail: bool = True, **opts):
+        vjp_N = self.field(torch.float64)
+        vjp_lnA = ctypes.c_double()
+        o, stt = default_opts(**opts), Stats()
+        st = self.lib.plc_map_vjp(
+            self._h, _ptr(s_map, self.n, torch.float64, "s_map"),
+            _ptr(w, self.n, torch.float64, "w", False), float(nbar),
+            _ptr(u, self.n, torch.float64, "u"), _ptr(vjp_N, self.n, torch.float64, "vjp_N"),
+            ctypes.byref(vjp_lnA), ctypes.byref(o), ctypes.byref(stt))
+        if raise_on_fail:
+            self._check(st)
+        return vjp_N, vjp_lnA.value, stt.as_dict()

@@ -1,0 +1,387 @@
+// capi.cu -- the extern "C" boundary of libplc (declared in include/plc.h).
+//
+// Validates every argument before anything is launched, owns the context's
+// device scratch, and turns CUDA failures into status codes (no exception
+// crosses the ABI).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "solver.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+plc_status fail(plc_ctx* c, plc_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  g_last_error = msg;
+  return st;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool valid_size(int n) {
+  if (n < 4 || n > 512 || (n & 1)) return false;
+  int m = n;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+// Radices for a length-n FFT: as many 8s as possible without leaving a lone
+// 2 (then 4s), then the 3s.
+plc::FftPlan make_plan(int n) {
+  plc::FftPlan p{};
+  p.n = n;
+  int a = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  int b = 0;
+  while (m % 3 == 0) { m /= 3; ++b; }
+  std::vector<int> r;
+  int q = a / 3, rem = a % 3;
+  if (rem == 1 && q >= 1) { q -= 1; rem = 4; }
+  for (int i = 0; i < q; ++i) r.push_back(8);
+  if (rem == 1) r.push_back(2);
+  if (rem == 2) r.push_back(4);
+  if (rem == 4) { r.push_back(4); r.push_back(4); }
+  for (int i = 0; i < b; ++i) r.push_back(3);
+  p.nst = (int)r.size();
+  for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
+  return p;
+}
+
+template <typename T> void dalloc(T** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    (void)cudaGetLastError();
+    throw std::bad_alloc();
+  }
+}
+
+void release(plc_ctx* c) {
+  void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->M64, c->M32, c->lk, c->lP,
+                  c->sc, c->partials, c->f_g, c->f_D, c->f_D32, c->f_r, c->f_x, c->f_p, c->f_Hp};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->sc_host) cudaFreeHost(c->sc_host);
+}
+
+void ensure_work_fields(plc_ctx* c) {
+  if (c->f_g) return;
+  const size_t b = sizeof(double) * c->n3();
+  dalloc(&c->f_g, b);
+  dalloc(&c->f_D, b);
+  dalloc(&c->f_D32, sizeof(float) * c->n3());
+  dalloc(&c->f_r, b);
+  dalloc(&c->f_x, b);
+  dalloc(&c->f_p, b);
+  dalloc(&c->f_Hp, b);
+}
+
+// Run `body`; map CUDA errors and allocation failures to status codes.
+template <typename F> plc_status guarded(plc_ctx* c, F body) {
+  try {
+    return body();
+  } catch (const plc::CudaError& e) {
+    return fail(c, PLC_ERR_CUDA, std::string(e.where) + ": " + cudaGetErrorString(e.code));
+  } catch (const std::bad_alloc&) {
+    return fail(c, PLC_ERR_OOM, "device allocation failed");
+  }
+}
+
+plc_status need_prior(plc_ctx* c) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  if (!c->have_prior) return fail(c, PLC_ERR_INVALID_ARG, "no prior: call plc_set_prior first");
+  return PLC_OK;
+}
+
+plc_status need_field(plc_ctx* c, const void* p, const char* name, bool required) {
+  if (!p) return required ? fail(c, PLC_ERR_INVALID_ARG, std::string(name) + " is NULL") : PLC_OK;
+  if (!aligned16(p)) return fail(c, PLC_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+  return PLC_OK;
+}
+
+#define PLC_TRY(expr)                 \
+  do {                                \
+    plc_status _s = (expr);           \
+    if (_s != PLC_OK) return _s;      \
+  } while (0)
+
+plc_opts resolve_opts(const plc_opts* o) {
+  plc_opts d;
+  plc_default_opts(&d);
+  return o ? *o : d;
+}
+
+plc_status check_opts(plc_ctx* c, const plc_opts& o) {
+  if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return fail(c, PLC_ERR_INVALID_ARG, "opts.tol must be > 0");
+  if (o.max_newton < 0 || o.max_cg < 1) return fail(c, PLC_ERR_INVALID_ARG, "bad iteration caps");
+  if (o.precond != 0 && o.precond != 1) return fail(c, PLC_ERR_INVALID_ARG, "opts.precond must be 0 or 1");
+  if (!(o.step_cap > 0.0) || !(o.eta_max > 0.0) || o.eta_max >= 1.0 || o.g0_norm < 0.0)
+    return fail(c, PLC_ERR_INVALID_ARG, "bad step_cap / eta_max / g0_norm");
+  if (o.cg_chunk < 1) return fail(c, PLC_ERR_INVALID_ARG, "opts.cg_chunk must be >= 1");
+  return PLC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* plc_status_string(int s) {
+  switch (s) {
+    case PLC_OK: return "PLC_OK";
+    case PLC_ERR_INVALID_ARG: return "PLC_ERR_INVALID_ARG";
+    case PLC_ERR_CUDA: return "PLC_ERR_CUDA";
+    case PLC_ERR_NOT_CONVERGED: return "PLC_ERR_NOT_CONVERGED";
+    case PLC_ERR_NONFINITE: return "PLC_ERR_NONFINITE";
+    case PLC_ERR_CG_BREAKDOWN: return "PLC_ERR_CG_BREAKDOWN";
+    case PLC_ERR_OOM: return "PLC_ERR_OOM";
+    default: return "PLC_ERR_UNKNOWN";
+  }
+}
+
+const char* plc_last_error(const plc_ctx* c) { return c ? c->err.c_str() : g_last_error.c_str(); }
+
+plc_status plc_default_opts(plc_opts* o) {
+  if (!o) return fail(nullptr, PLC_ERR_INVALID_ARG, "opts is NULL");
+  o->tol = 1e-6;
+  o->max_newton = 200;
+  o->max_cg = 1000;
+  o->precond = 1;
+  o->g0_norm = 0.0;
+  o->step_cap = 2.0;
+  o->eta_max = 0.5;
+  o->cg_chunk = 8;
+  return PLC_OK;
+}
+
+plc_status plc_create(plc_ctx** out, int n, double box, int precision, void* stream) {
+  if (!out) return fail(nullptr, PLC_ERR_INVALID_ARG, "ctx out-pointer is NULL");
+  *out = nullptr;
+  if (!valid_size(n))
+    return fail(nullptr, PLC_ERR_INVALID_ARG, "n must be even, 4..512, with prime factors 2 and 3 only");
+  if (!(box > 0.0) || !std::isfinite(box)) return fail(nullptr, PLC_ERR_INVALID_ARG, "box must be > 0");
+  if (precision != PLC_FP64 && precision != PLC_MIXED)
+    return fail(nullptr, PLC_ERR_INVALID_ARG, "precision must be PLC_FP64 or PLC_MIXED");
+  plc_ctx* c = new (std::nothrow) plc_ctx();
+  if (!c) return fail(nullptr, PLC_ERR_OOM, "host allocation failed");
+  c->n = n;
+  c->box = box;
+  c->precision = precision;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->plan = make_plan(n);
+  plc_status st = guarded(c, [&]() -> plc_status {
+    int dev = 0;
+    plc::check(cudaGetDevice(&dev), "cudaGetDevice");
+    plc::check(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const size_t h = n / 2 + 1;
+    const size_t spec = sizeof(double2) * h * n * n;
+    dalloc(&c->specA, spec);
+    dalloc(&c->specB, spec);
+    dalloc(&c->tw64, sizeof(double2) * n);
+    dalloc(&c->tw32, sizeof(float2) * n);
+    dalloc(&c->sc, sizeof(plc::DevScalars));
+    plc::check(cudaMallocHost(reinterpret_cast<void**>(&c->sc_host), sizeof(plc::DevScalars)),
+               "cudaMallocHost");
+    const size_t xi_blocks = (size_t)((n + 15) / 16) * n;
+    c->partial_blocks = std::max(xi_blocks, (size_t)c->sms * 8);
+    dalloc(&c->partials, sizeof(double) * plc::kMaxRed * c->partial_blocks);
+    // twiddles W_n^m = exp(-2 pi i m / n), from the FP64 host sin/cos
+    std::vector<double2> t64(n);
+    std::vector<float2> t32(n);
+    for (int m = 0; m < n; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / (double)n;
+      t64[m] = make_double2(std::cos(ang), -std::sin(ang));
+      t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
+    }
+    plc::check(cudaMemcpyAsync(c->tw64, t64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
+    plc::check(cudaMemcpyAsync(c->tw32, t32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
+    plc::check(cudaMemsetAsync(c->sc, 0, sizeof(plc::DevScalars), c->stream), "clear scalars");
+    plc::check(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return PLC_OK;
+  });
+  if (st != PLC_OK) {
+    g_last_error = c->err;
+    release(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return PLC_OK;
+}
+
+plc_status plc_destroy(plc_ctx* c) {
+  if (!c) return PLC_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  release(c);
+  delete c;
+  return PLC_OK;
+}
+
+plc_status plc_set_prior(plc_ctx* c, const double* k, const double* P, int nk, double mu,
+                         double inv_lambda_dc) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  if (!k || !P || nk < 2) return fail(c, PLC_ERR_INVALID_ARG, "need k, P arrays with nk >= 2");
+  for (int i = 0; i < nk; ++i) {
+    if (!(k[i] > 0.0) || !std::isfinite(k[i]) || !(P[i] > 0.0) || !std::isfinite(P[i]))
+      return fail(c, PLC_ERR_INVALID_ARG, "k and P must be finite and > 0");
+    if (i && !(k[i] > k[i - 1])) return fail(c, PLC_ERR_INVALID_ARG, "k must be strictly ascending");
+  }
+  const double kf = 2.0 * M_PI / c->box;
+  const double kmax = std::sqrt(3.0) * M_PI * c->n / c->box;
+  if (k[0] > kf * (1.0 + 1e-12) || k[nk - 1] < kmax * (1.0 - 1e-12))
+    return fail(c, PLC_ERR_INVALID_ARG, "P(k) table must cover [2 pi / L, sqrt(3) pi n / L]");
+  if (!std::isfinite(mu)) return fail(c, PLC_ERR_INVALID_ARG, "mu must be finite");
+  if (!(inv_lambda_dc >= 0.0) || !std::isfinite(inv_lambda_dc))
+    return fail(c, PLC_ERR_INVALID_ARG, "inv_lambda_dc must be finite and >= 0");
+  return guarded(c, [&]() -> plc_status {
+    const int half = c->n / 2;
+    const int nm2 = 3 * half * half + 1;
+    if (c->nm2 != nm2) {
+      if (c->M64) cudaFree(c->M64);
+      if (c->M32) cudaFree(c->M32);
+      c->M64 = nullptr;
+      c->M32 = nullptr;
+      dalloc(&c->M64, sizeof(double) * nm2);
+      dalloc(&c->M32, sizeof(float) * nm2);
+      c->nm2 = nm2;
+    }
+    if (c->nk_cap < nk) {
+      if (c->lk) cudaFree(c->lk);
+      if (c->lP) cudaFree(c->lP);
+      c->lk = nullptr;
+      c->lP = nullptr;
+      dalloc(&c->lk, sizeof(double) * nk);
+      dalloc(&c->lP, sizeof(double) * nk);
+      c->nk_cap = nk;
+    }
+    std::vector<double> lk(nk), lP(nk);
+    for (int i = 0; i < nk; ++i) {
+      lk[i] = std::log(k[i]);
+      lP[i] = std::log(P[i]);
+    }
+    c->mu = mu;
+    c->inv_dc = inv_lambda_dc;
+    c->have_prior = false;
+    plc::build_prior(c, lk.data(), lP.data(), nk);
+    c->have_prior = true;
+    c->err.clear();
+    return PLC_OK;
+  });
+}
+
+plc_status plc_prior_apply(plc_ctx* c, const void* x, void* y) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, x, "x", true));
+  PLC_TRY(need_field(c, y, "y", true));
+  return guarded(c, [&]() -> plc_status {
+    if (c->precision == PLC_FP64)
+      plc::prior_apply<double>(c, static_cast<const double*>(x), static_cast<double*>(y));
+    else
+      plc::prior_apply<float>(c, static_cast<const float*>(x), static_cast<float*>(y));
+    return PLC_OK;
+  });
+}
+
+plc_status plc_logpost_grad(plc_ctx* c, const void* s, const int32_t* N, const void* w,
+                            double nbar, double* neg_logpost, void* grad) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, s, "s", true));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, grad, "grad", false));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  return guarded(c, [&]() -> plc_status {
+    plc::reset_ticket(c);
+    if (c->precision == PLC_FP64)
+      plc::grad<double>(c, static_cast<const double*>(s), static_cast<const double*>(w), N, nbar,
+                        static_cast<double*>(grad), nullptr, nullptr);
+    else
+      plc::grad<float>(c, static_cast<const float*>(s), static_cast<const float*>(w), N, nbar,
+                       static_cast<float*>(grad), nullptr, nullptr);
+    if (neg_logpost) {
+      plc::read_scalars(c);
+      const double* r = c->sc_host->red;
+      *neg_logpost = 0.5 * r[0] + r[1];
+      if (!std::isfinite(*neg_logpost)) return fail(c, PLC_ERR_NONFINITE, "non-finite -ln P");
+    }
+    return PLC_OK;
+  });
+}
+
+plc_status plc_hessvec(plc_ctx* c, const void* s, const void* w, double nbar, const void* v,
+                       void* Hv) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, s, "s", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, v, "v", true));
+  PLC_TRY(need_field(c, Hv, "Hv", true));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  return guarded(c, [&]() -> plc_status {
+    if (c->precision == PLC_FP64)
+      plc::hessvec_s<double>(c, static_cast<const double*>(s), static_cast<const double*>(w), nbar,
+                             static_cast<const double*>(v), static_cast<double*>(Hv));
+    else
+      plc::hessvec_s<float>(c, static_cast<const float*>(s), static_cast<const float*>(w), nbar,
+                            static_cast<const float*>(v), static_cast<float*>(Hv));
+    return PLC_OK;
+  });
+}
+
+plc_status plc_newton_krylov_map(plc_ctx* c, const int32_t* N, const void* w, double nbar,
+                                 double* s_inout, const plc_opts* opts, plc_stats* stats) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, s_inout, "s_inout", true));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  const plc_opts o = resolve_opts(opts);
+  PLC_TRY(check_opts(c, o));
+  return guarded(c, [&]() -> plc_status {
+    ensure_work_fields(c);
+    plc_status st;
+    if (c->precision == PLC_FP64)
+      st = plc::newton_map<double>(c, N, static_cast<const double*>(w), nbar, s_inout, o, stats);
+    else
+      st = plc::newton_map<float>(c, N, static_cast<const double*>(w), nbar, s_inout, o, stats);
+    if (st == PLC_ERR_NOT_CONVERGED) fail(c, st, "Newton iteration cap reached");
+    else if (st == PLC_ERR_NONFINITE) fail(c, st, "non-finite gradient or objective");
+    else if (st == PLC_ERR_CG_BREAKDOWN) fail(c, st, "CG breakdown on the first step");
+    else c->err.clear();
+    return st;
+  });
+}
+
+plc_status plc_map_vjp(plc_ctx* c, const double* s_map, const void* w, double nbar,
+                       const double* u, double* vjp_N, double* vjp_lnA, const plc_opts* opts,
+                       plc_stats* stats) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, s_map, "s_map", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, u, "u", true));
+  PLC_TRY(need_field(c, vjp_N, "vjp_N", false));
+  if (!vjp_N && !vjp_lnA) return fail(c, PLC_ERR_INVALID_ARG, "no output requested");
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  const plc_opts o = resolve_opts(opts);
+  PLC_TRY(check_opts(c, o));
+  return guarded(c, [&]() -> plc_status {
+    ensure_work_fields(c);
+    plc_status st;
+    if (c->precision == PLC_FP64)
+      st = plc::map_vjp<double>(c, s_map, static_cast<const double*>(w), nbar, u, vjp_N, vjp_lnA, o, stats);
+    else
+      st = plc::map_vjp<float>(c, s_map, static_cast<const double*>(w), nbar, u, vjp_N, vjp_lnA, o, stats);
+    if (st != PLC_OK) fail(c, st, "adjoint CG did not reach the tolerance");
+    else c->err.clear();
+    return st;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// common.cuh -- shared device building blocks of libplc (sm_103a).
+//
+// * complex arithmetic on float2 / double2;
+// * the radix-2/3/4/8 DFT butterflies and one Stockham autosort stage for a
+//   batch of lines held in shared memory (the 3D FFT of the prior operator,
+//   Sec. 2.2: S is a convolution, applied through FFTs as in Sec. 3);
+// * a deterministic grid-wide reduction: warp shuffles, a per-block partial,
+//   and a fixed-order final sum by the last block to finish.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace plc {
+
+constexpr int kThreads = 256;          // threads per block of every kernel
+constexpr int kMaxStages = 12;
+constexpr int kMaxRed = 8;             // values per reduction
+
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cpx = typename CplxOf<T>::type;
+
+// Lines per shared-memory tile: 128 bytes of complex values per tile row.
+template <typename T> struct Tile { static constexpr int L = 128 / (2 * (int)sizeof(T)); };
+
+struct FftPlan {
+  int n;                     // transform length (the grid side)
+  int nst;                   // number of radix stages
+  int rad[kMaxStages];       // radix of each stage (2, 3, 4 or 8)
+};
+
+// Device-resident scalars of the solver (one instance per context).
+struct DevScalars {
+  double red[kMaxRed];       // results of the last reduction
+  double rz;                 // r^T M^-1 r
+  double alpha, beta;
+  double rr;                 // ||r||^2
+  double bnorm2;             // ||b||^2
+  double rtol2;              // CG stops at ||r||^2 <= rtol2 * bnorm2
+  double pHp;
+  int iter, max_iter;
+  int done, breakdown;
+  unsigned ticket;           // last-block-done counter
+  int pad;
+};
+
+template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {
+  C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return cmk<C>(a.x * s, a.y * s); }
+// multiply by SIGN * i
+template <int SIGN, typename C> __device__ __forceinline__ C cmul_si(C a) {
+  return SIGN > 0 ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs X_k = sum_j v_j exp(SIGN 2 pi i j k / R) on registers.
+// ---------------------------------------------------------------------------
+template <typename T, int SIGN> struct Dft {
+  using C = cpx<T>;
+  static __device__ __forceinline__ void r2(C* v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b); v[1] = csub(a, b);
+  }
+  static __device__ __forceinline__ void r3(C* v) {
+    const T h = (T)0.86602540378443864676;   // sin(2 pi / 3)
+    C s = cadd(v[1], v[2]);
+    C d = csub(v[1], v[2]);
+    C m = cmk<C>(v[0].x - (T)0.5 * s.x, v[0].y - (T)0.5 * s.y);
+    C t = cmul_si<SIGN>(cscale(d, h));
+    v[0] = cadd(v[0], s);
+    v[1] = cadd(m, t);
+    v[2] = csub(m, t);
+  }
+  static __device__ __forceinline__ void r4(C* v) {
+    C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    C c = cadd(v[1], v[3]), d = cmul_si<SIGN>(csub(v[1], v[3]));
+    v[0] = cadd(a, c); v[2] = csub(a, c);
+    v[1] = cadd(b, d); v[3] = csub(b, d);
+  }
+  static __device__ __forceinline__ void r8(C* v) {
+    const T q = (T)0.70710678118654752440;    // 1/sqrt(2)
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    r4(e); r4(o);
+    // o_k *= exp(SIGN 2 pi i k / 8)
+    C o1 = cmk<C>(q * (o[1].x - SIGN * o[1].y), q * (o[1].y + SIGN * o[1].x));
+    C o2 = cmul_si<SIGN>(o[2]);
+    C o3 = cmk<C>(q * (-o[3].x - SIGN * o[3].y), q * (-o[3].y + SIGN * o[3].x));
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+  }
+};
+
+// One Stockham autosort stage of radix R on `nl` lines of length N held in
+// shared memory; element i of line c lives at buf[i * P + c].  Ns is the
+// product of the radices already applied.  Butterfly j of a line reads
+// elements j + r N/R, twiddles them by W_{Ns R}^{r k} (k = j mod Ns), and
+// writes elements (j - k) R + k + r Ns.  tw[m] = exp(-2 pi i m / N).
+template <typename T, int R, int SIGN, int L>
+__device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
+                                               cpx<T>* __restrict__ out, int N,
+                                               int Ns, int nl, int P,
+                                               const cpx<T>* __restrict__ tw) {
+  using C = cpx<T>;
+  const int NR = N / R;
+  const int tstep = N / (Ns * R);
+  const int total = L * NR;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int c = b % L;
+    const int j = b / L;
+    if (c >= nl) continue;
+    const int k = j % Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[(j + r * NR) * P + c];
+    if (k != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = tw[r * k * tstep];
+        if (SIGN > 0) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    if (R == 2) Dft<T, SIGN>::r2(v);
+    if (R == 3) Dft<T, SIGN>::r3(v);
+    if (R == 4) Dft<T, SIGN>::r4(v);
+    if (R == 8) Dft<T, SIGN>::r8(v);
+    const int d = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[(d + r * Ns) * P + c] = v[r];
+  }
+}
+
+// Full length-N transform of `nl` (<= L) lines.  On return `a` points at the
+// result and `b` at the free buffer.  Ends with a __syncthreads().
+template <typename T, int SIGN, int L>
+__device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan,
+                                          int nl, int P, const cpx<T>* tw) {
+  int Ns = 1;
+  const int N = plan.n;
+  for (int s = 0; s < plan.nst; ++s) {
+    const int R = plan.rad[s];
+    if (R == 8) stockham_stage<T, 8, SIGN, L>(a, b, N, Ns, nl, P, tw);
+    else if (R == 4) stockham_stage<T, 4, SIGN, L>(a, b, N, Ns, nl, P, tw);
+    else if (R == 2) stockham_stage<T, 2, SIGN, L>(a, b, N, Ns, nl, P, tw);
+    else stockham_stage<T, 3, SIGN, L>(a, b, N, Ns, nl, P, tw);
+    __syncthreads();
+    cpx<T>* t = a; a = b; b = t;
+    Ns *= R;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic grid reduction.  Every block calls block_reduce_finish with
+// its per-thread accumulators; the last block to arrive sums the per-block
+// partials in block order and calls fin(totals, scalars) on thread 0.
+// ---------------------------------------------------------------------------
+struct RedArgs {
+  double* partials;          // [gridDim.x * gridDim.y * gridDim.z][kMaxRed]
+  DevScalars* sc;
+};
+
+// MAXMASK bit j set: value j is reduced with max, otherwise with +.
+template <unsigned MAXMASK>
+__device__ __forceinline__ double red_op(int j, double a, double b) {
+  return ((MAXMASK >> j) & 1u) ? fmax(a, b) : a + b;
+}
+template <unsigned MAXMASK>
+__device__ __forceinline__ double red_identity(int j) {
+  return ((MAXMASK >> j) & 1u) ? -INFINITY : 0.0;
+}
+
+template <int NV, unsigned MAXMASK>
+__device__ __forceinline__ void warp_reduce(double* v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = red_op<MAXMASK>(j, v[j], __shfl_down_sync(0xffffffffu, v[j], o));
+  }
+}
+
+// Reduce v[NV] over the block in a fixed order; thread 0 gets the result.
+template <int NV, unsigned MAXMASK>
+__device__ __forceinline__ void block_reduce(double* v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  warp_reduce<NV, MAXMASK>(v);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[warp * NV + j] = v[j];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = lane < nw ? sh[lane * NV + j] : red_identity<MAXMASK>(j);
+    warp_reduce<NV, MAXMASK>(v);
+  }
+  __syncthreads();
+}
+
+template <int NV, unsigned MAXMASK, typename Fin>
+__device__ __forceinline__ void block_reduce_finish(double* v, const RedArgs& ra, Fin fin) {
+  __shared__ double sh[32 * kMaxRed];
+  __shared__ int is_last;
+  const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  block_reduce<NV, MAXMASK>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) ra.partials[(size_t)bid * kMaxRed + j] = v[j];
+    __threadfence();
+    unsigned t = atomicAdd(&ra.sc->ticket, 1u);
+    is_last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = red_identity<MAXMASK>(j);
+  for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      acc[j] = red_op<MAXMASK>(j, acc[j], __ldcg(ra.partials + (size_t)b * kMaxRed + j));
+  }
+  block_reduce<NV, MAXMASK>(acc, sh);
+  if (threadIdx.x == 0) {
+    fin(acc, ra.sc);
+    ra.sc->ticket = 0u;
+    __threadfence();
+  }
+}
+
+// Grid size for element-wise kernels: a fixed multiple of the SM count so
+// that reductions are reproducible for a given problem size.
+inline int pointwise_blocks(long long nelem, int sms) {
+  long long want = (nelem + kThreads * 4 - 1) / (kThreads * 4);
+  long long cap = (long long)sms * 8;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+}  // namespace plc

@@ -1,0 +1,96 @@
+// ctx.h -- host-side state of a libplc context and the internal launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/plc.h"
+#include "common.cuh"
+
+struct plc_ctx {
+  int n = 0;
+  double box = 0.0;
+  int precision = PLC_FP64;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  plc::FftPlan plan{};
+
+  // FFT scratch: two half-spectra sized for double2 (float2 reuses them).
+  void* specA = nullptr;
+  void* specB = nullptr;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+
+  // Prior: inverse eigenvalue per |m|^2, its FP32 copy, ln-tables.
+  double* M64 = nullptr;
+  float* M32 = nullptr;
+  int nm2 = 0;
+  double* lk = nullptr;
+  double* lP = nullptr;
+  int nk_cap = 0;
+  bool have_prior = false;
+  double mu = 0.0;
+  double inv_dc = 0.0;
+  double jac_c = 0.0;          // (S^-1)_ii
+
+  // Reductions and device scalars.
+  plc::DevScalars* sc = nullptr;
+  plc::DevScalars* sc_host = nullptr;   // pinned
+  double* partials = nullptr;
+  size_t partial_blocks = 0;
+
+  // Solver work fields (sized for double), allocated on first use.
+  void* f_g = nullptr;
+  void* f_D = nullptr;
+  void* f_D32 = nullptr;
+  void* f_r = nullptr;
+  void* f_x = nullptr;
+  void* f_p = nullptr;
+  void* f_Hp = nullptr;
+
+  std::string err;
+
+  size_t n3() const { return (size_t)n * n * n; }
+};
+
+namespace plc {
+
+// Error plumbing: a CUDA failure is recorded on the context and turned into
+// PLC_ERR_CUDA by the caller.
+struct CudaError {
+  cudaError_t code;
+  const char* where;
+};
+void check(cudaError_t e, const char* where);   // throws CudaError
+
+// Spectral pipelines (five passes).  T = field type of the FFT.
+template <typename T> void prior_apply(plc_ctx* c, const T* x, T* y);
+template <typename T> void hessvec_s(plc_ctx* c, const T* s, const T* w, double nbar,
+                                     const T* v, T* out);
+template <typename T> void grad(plc_ctx* c, const T* s, const T* w, const int32_t* N,
+                                double nbar, T* g, T* D, float* D32);
+template <typename T, typename TX> void grad_step(plc_ctx* c, T* s, const TX* xi, double tau,
+                                                  const T* w, const int32_t* N, double nbar,
+                                                  T* g, T* D, float* D32);
+template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac);
+template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL* lam);
+
+// Element-wise kernels.
+template <typename TC, typename TB> void cg_init(plc_ctx* c, const TB* b, bool negate,
+                                                 const TC* D, TC* r, TC* x, double rtol2,
+                                                 int max_iter, bool jac);
+template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
+                                      const TC* D, bool jac);
+template <typename TC, typename TG> void dirstats(plc_ctx* c, const TC* xi, const TG* g,
+                                                  const TC* r, const TG* D, const int32_t* N);
+template <typename TC, typename TG> void trial(plc_ctx* c, const TC* xi, const TG* D, double tau);
+template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D);
+template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* dst);
+
+void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int nk);
+void reset_ticket(plc_ctx* c);
+void read_scalars(plc_ctx* c);    // copies sc -> sc_host and synchronises
+
+}  // namespace plc

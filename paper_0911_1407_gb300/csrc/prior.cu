@@ -1,0 +1,81 @@
+// prior.cu -- device set-up of the prior operator (Sec. 2.2): the inverse
+// eigenvalue 1/(lambda n^3) for every |m|^2 of the grid and the Jacobi
+// constant (S^-1)_ii; plus the small host helpers shared by the solver.
+#include "launch.cuh"
+
+namespace plc {
+
+// ----------------------------- prior set-up -------------------------------
+// M[m2] = 1 / (lambda n^3) for |m|^2 = m2, lambda = P(|k|) n^3 / L^3 with
+// |k| = (2 pi / L) sqrt(m2) and P linear in (ln k, ln P) between the table
+// points lk = ln k, lP = ln P.  M[0] = inv_lambda_dc / n^3.
+__global__ void k_build_multiplier(double* __restrict__ M64, float* __restrict__ M32, int nm2,
+                                   int n, double box, const double* __restrict__ lk,
+                                   const double* __restrict__ lP, int nk, double inv_dc) {
+  const double n3 = (double)n * n * n;
+  for (int m2 = blockIdx.x * blockDim.x + threadIdx.x; m2 < nm2; m2 += gridDim.x * blockDim.x) {
+    double v;
+    if (m2 == 0) {
+      v = inv_dc / n3;
+    } else {
+      const double lnk = log(2.0 * 3.14159265358979323846 / box) + 0.5 * log((double)m2);
+      int lo = 0, hi = nk - 1;                 // largest j with lk[j] <= lnk
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (lk[mid] <= lnk) lo = mid; else hi = mid;
+      }
+      const double t = (lnk - lk[lo]) / (lk[lo + 1] - lk[lo]);
+      const double lnP = lP[lo] + t * (lP[lo + 1] - lP[lo]);
+      const double lam = exp(lnP) * n3 / (box * box * box);
+      v = 1.0 / (lam * n3);
+    }
+    M64[m2] = v;
+    M32[m2] = (float)v;
+  }
+}
+
+// (S^-1)_ii = n^-3 sum_k 1/lambda_k = sum over all n^3 modes of M[|m|^2].
+__global__ void __launch_bounds__(kThreads)
+k_jacobi_constant(const double* __restrict__ M64, int n, RedArgs ra) {
+  double acc[1] = {0.0};
+  const size_t n3 = (size_t)n * n * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % n), ky = (int)((i / n) % n), kz = (int)(i / ((size_t)n * n));
+    const int mx = min(kx, n - kx), my = min(ky, n - ky), mz = min(kz, n - kz);
+    acc[0] += M64[mx * mx + my * my + mz * mz];
+  }
+  block_reduce_finish<1, 0u>(acc, ra, FinStore<1>{});
+}
+
+void check(cudaError_t e, const char* where) {
+  if (e != cudaSuccess) throw CudaError{e, where};
+}
+
+void reset_ticket(plc_ctx* c) {
+  check(cudaMemsetAsync(&c->sc->ticket, 0, sizeof(unsigned), c->stream), "reset ticket");
+}
+
+void read_scalars(plc_ctx* c) {
+  check(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream),
+        "read scalars");
+  check(cudaStreamSynchronize(c->stream), "stream synchronize");
+}
+
+void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int nk) {
+  check(cudaMemcpyAsync(c->lk, lk_host, sizeof(double) * nk, cudaMemcpyHostToDevice, c->stream),
+        "copy ln k");
+  check(cudaMemcpyAsync(c->lP, lP_host, sizeof(double) * nk, cudaMemcpyHostToDevice, c->stream),
+        "copy ln P");
+  const int nb = (c->nm2 + kThreads - 1) / kThreads;
+  k_build_multiplier<<<nb, kThreads, 0, c->stream>>>(c->M64, c->M32, c->nm2, c->n, c->box, c->lk,
+                                                      c->lP, nk, c->inv_dc);
+  check(cudaGetLastError(), "k_build_multiplier");
+  reset_ticket(c);
+  k_jacobi_constant<<<pw_blocks(c), kThreads, 0, c->stream>>>(c->M64, c->n, red_args(c));
+  check(cudaGetLastError(), "k_jacobi_constant");
+  read_scalars(c);
+  c->jac_c = c->sc_host->red[0];
+}
+
+}  // namespace plc

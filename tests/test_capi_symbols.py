@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every function plc.h declares.
+
+Runs without a GPU: only calls that validate arguments before touching CUDA
+(plc_create with an invalid size, plc_default_opts, plc_status_string) are
+made.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "plc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(plc_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0911_1407_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("plc_logpost_grad", "plc_hessvec", "plc_newton_krylov_map", "plc_map_vjp",
+                 "plc_prior_apply", "plc_create", "plc_set_prior"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in plc.h but not exported"
+
+
+def test_binding_covers_every_symbol():
+    from paper_0911_1407_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_functions()
+
+
+def test_validation_without_gpu(lib):
+    h = ctypes.c_void_p()
+    lib.plc_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_void_p]
+    for bad_n in (0, 7, 10, 14, 1024):
+        assert lib.plc_create(ctypes.byref(h), bad_n, 100.0, 0, None) == 1
+    assert lib.plc_create(ctypes.byref(h), 16, -1.0, 0, None) == 1
+    assert lib.plc_create(ctypes.byref(h), 16, 100.0, 5, None) == 1
+    lib.plc_status_string.restype = ctypes.c_char_p
+    assert lib.plc_status_string(3) == b"PLC_ERR_NOT_CONVERGED"
+    from paper_0911_1407_gb300._lib import Opts
+    o = Opts()
+    assert lib.plc_default_opts(ctypes.byref(o)) == 0
+    assert o.tol == 1e-6 and o.precond == 1 and o.max_cg == 1000

@@ -1,0 +1,119 @@
+"""GPU parity of the Newton-Krylov MAP and its adjoint against the oracle.
+
+Bars: FP64 GPU MAP within a per-voxel relative error of 1e-10
+(|s - s_ref| / max(|s_ref|, 1)) of the oracle, both converged to
+||g|| / ||g0|| < 1e-12.  Mixed precision stopped at 1e-6: max-abs error
+<= 1e-4 and relative-L2 <= 1e-5 against the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import plc as orc
+from paper_0911_1407_gb300 import mocks
+from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plc():
+    return ensure_lib()
+
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_map(key, m, tol=1e-12):
+    if key not in _ORACLE_CACHE:
+        p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab)
+        _ORACLE_CACHE[key] = (p, orc.newton_krylov_map(p, tol=tol))
+    return _ORACLE_CACHE[key]
+
+
+def _mock(key):
+    if key == "plain32":
+        return mocks.make_mock(mocks.WORKLOADS["plain32"])
+    if key == "sel24":
+        return small_mock(24, "radial_masked", sigma=1.3, nbar=1.0)
+    if key == "sel48":
+        return small_mock(48, "radial_masked", sigma=1.5, nbar=0.5)
+    raise KeyError(key)
+
+
+def _gpu_map(plc, m, precision, tol, **kw):
+    c = plc.Context(m.n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    r = c.newton_krylov_map(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=tol, **kw)
+    return host(r.s), r.stats
+
+
+@pytest.mark.parametrize("key", ["plain32", "sel24"])
+def test_map_fp64_matches_oracle(plc, key):
+    m = _mock(key)
+    p, ref = _oracle_map(key, m)
+    assert ref.converged
+    s, st = _gpu_map(plc, m, "fp64", 1e-12)
+    assert st["grad_rel"] < 1e-12
+    err = np.abs(s - ref.s) / np.maximum(np.abs(ref.s), 1.0)
+    assert err.max() <= 1e-10
+    # DC of the gradient vanishes at the MAP: sum w nbar e^s = sum N
+    D = p.wn * np.exp(s)
+    assert abs(D.sum() - m.N.sum()) <= 1e-9 * m.N.sum()
+
+
+@pytest.mark.parametrize("key", ["plain32", "sel24", "sel48"])
+def test_map_mixed_matches_oracle(plc, key):
+    m = _mock(key)
+    _, ref = _oracle_map(key, m)
+    s, st = _gpu_map(plc, m, "mixed", 1e-6)
+    assert st["grad_rel"] < 1e-6
+    assert np.max(np.abs(s - ref.s)) <= 1e-4
+    assert rel_l2(s, ref.s) <= 1e-5
+
+
+def test_map_diagonal_prior_closed_form(plc):
+    n, box, sigma2 = 16, 80.0, 0.9
+    rng = np.random.default_rng(7)
+    N = rng.poisson(2.5, size=(n, n, n)).astype(np.int32)
+    N[0, 0, 0] = 60
+    w = rng.uniform(0.05, 1.0, size=(n, n, n))
+    nbar, mu = 1.4, -0.45
+    k = np.array([0.5 * 2 * math.pi / box, 2 * math.sqrt(3) * math.pi * n / box])
+    P = np.full(2, sigma2 * box ** 3 / n ** 3)
+    c = plc.Context(n, box, "fp64")
+    c.set_prior(k, P, mu, 1.0 / sigma2)
+    r = c.newton_krylov_map(dev(N, torch.int32), dev(w, torch.float64), nbar, tol=1e-13)
+    exact = orc.map_closed_form_diagonal(N, w, nbar, mu, sigma2)
+    err = np.abs(host(r.s) - exact) / np.maximum(np.abs(exact), 1.0)
+    assert err.max() <= 1e-10
+
+
+def test_map_resume_and_cap(plc):
+    m = _mock("plain32")
+    c = plc.Context(m.n, m.box, "fp64")
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    Nd = dev(m.N, torch.int32)
+    r1 = c.newton_krylov_map(Nd, None, m.nbar, tol=1e-12, max_newton=2, raise_on_fail=False)
+    assert r1.status == 3 and r1.stats["newton_iters"] == 2
+    # resume from the last iterate with the original ||g0||
+    r2 = c.newton_krylov_map(Nd, None, m.nbar, s=r1.s, tol=1e-12, g0_norm=r1.stats["g0_norm"])
+    _, ref = _oracle_map("plain32", m)
+    assert np.max(np.abs(host(r2.s) - ref.s) / np.maximum(np.abs(ref.s), 1)) <= 1e-10
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_vjp_matches_oracle(plc, precision, bar):
+    m = small_mock(16, "uniform", sigma=1.0, nbar=2.0)
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab)
+    ref = orc.newton_krylov_map(p, tol=1e-13)
+    u = np.random.default_rng(2).standard_normal(m.N.shape)
+    lam_ref, lnA_ref, _ = orc.map_vjp(ref.s, u, p, rtol=1e-13)
+    c = plc.Context(m.n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    vN, vA, st = c.map_vjp(dev(ref.s, torch.float64), None, m.nbar, dev(u, torch.float64), tol=tol)
+    assert rel_l2(host(vN), lam_ref) <= bar
+    assert abs(vA - lnA_ref) <= bar * abs(lnA_ref)

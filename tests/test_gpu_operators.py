@@ -1,0 +1,145 @@
+"""GPU parity of the operators against the FP64 oracle (through the C ABI).
+
+Sizes span several tiles and a ragged tail: tiles are 8 (FP64) / 16 (FP32)
+complex lines and 16 / 32 real rows, so n = 24, 40-free sizes like 48 and 96
+leave partial tiles along z, y and the n/2+1 kx lines; n = 4 and 6 are
+smaller than one tile.  FP64 bar: relative error <= 1e-12 (an FFT round trip
+of length n^3 in double accumulates a few 1e-15 per stage).  FP32 bar
+(PLC_MIXED operators): relative L2 <= 1e-5, from eps32 = 6e-8 times the
+~log2(n^3) <= 27 butterfly stages of the two transforms and the pointwise
+tail, with margin.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import plc as orc
+from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock, pk_table_for
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [4, 6, 8, 12, 24, 48, 96]
+
+
+@pytest.fixture(scope="module")
+def plc():
+    return ensure_lib()
+
+
+def _ctx(plc, n, box, precision, mu=-0.3, dc=0.0, seed=0):
+    c = plc.Context(n, box, precision)
+    k, P = pk_table_for(n, box, seed=seed)
+    c.set_prior(k, P, mu, dc)
+    inv = orc.inverse_eigenvalues(n, box, k, P, dc)
+    return c, inv
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_prior_apply(plc, n, precision):
+    box = 7.0 * n
+    c, inv = _ctx(plc, n, box, precision, dc=0.37)
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((n, n, n))
+    ref = orc.apply_Sinv(x, inv)
+    y = host(c.prior_apply(dev(x, c.real)))
+    if precision == "fp64":
+        assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+    else:
+        assert rel_l2(y, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n,mode", [(32, (0, 0, 1)), (32, (16, 3, 7)), (24, (12, 12, 12)),
+                                    (48, (5, 20, 24))])
+def test_single_mode_eigenvalue(plc, n, mode):
+    box = 100.0
+    c, inv = _ctx(plc, n, box, "fp64")
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    f = np.cos(2 * np.pi * (mode[0] * z + mode[1] * y + mode[2] * x) / n + 0.1)
+    out = host(c.prior_apply(dev(f, torch.float64)))
+    lam_inv = inv[mode]
+    assert np.max(np.abs(out - lam_inv * f)) <= 1e-12 * lam_inv
+
+
+@pytest.mark.parametrize("n,selection", [(8, "uniform"), (24, "radial_masked"), (48, "uniform")])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_logpost_grad(plc, n, selection, precision):
+    m = small_mock(n, selection)
+    c = plc.Context(n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, n, m.box, m.k_tab, m.P_tab)
+    rng = np.random.default_rng(3)
+    s = m.mu + 0.7 * rng.standard_normal((n, n, n))
+    f_ref = orc.neg_log_posterior(s, p)
+    g_ref = orc.gradient(s, p)
+    f, g = c.logpost_grad(dev(s, c.real), dev(m.N, torch.int32), dev(m.w, c.real), m.nbar)
+    g = host(g)
+    if precision == "fp64":
+        assert abs(f - f_ref) <= 1e-12 * abs(f_ref)
+        assert np.max(np.abs(g - g_ref)) <= 1e-11 * np.max(np.abs(g_ref))
+    else:
+        # s itself is rounded to FP32: compare with the oracle at the rounded s
+        s32 = s.astype(np.float32).astype(np.float64)
+        assert abs(f - orc.neg_log_posterior(s32, p)) <= 1e-6 * abs(f_ref)
+        assert rel_l2(g, orc.gradient(s32, p)) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [6, 24, 48, 96])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hessvec(plc, n, precision):
+    m = small_mock(n, "radial_masked" if n >= 24 else "uniform")
+    c = plc.Context(n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, n, m.box, m.k_tab, m.P_tab)
+    rng = np.random.default_rng(4)
+    s = m.mu + 0.7 * rng.standard_normal((n, n, n))
+    v = rng.standard_normal((n, n, n))
+    if precision == "mixed":
+        s = s.astype(np.float32).astype(np.float64)
+    ref = orc.hessvec(s, v, p)
+    out = host(c.hessvec(dev(s, c.real), dev(m.w, c.real), m.nbar, dev(v, c.real)))
+    if precision == "fp64":
+        assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
+    else:
+        assert rel_l2(out, ref) <= 1e-5
+
+
+def test_hessian_symmetric_and_pd_on_gpu(plc):
+    n = 32
+    m = small_mock(n)
+    c = plc.Context(n, m.box, "fp64")
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    rng = np.random.default_rng(5)
+    s = dev(m.mu + 0.5 * rng.standard_normal((n,) * 3), torch.float64)
+    u = dev(rng.standard_normal((n,) * 3), torch.float64)
+    v = dev(rng.standard_normal((n,) * 3), torch.float64)
+    a = float((u * c.hessvec(s, None, m.nbar, v)).sum())
+    b = float((v * c.hessvec(s, None, m.nbar, u)).sum())
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert float((v * c.hessvec(s, None, m.nbar, v)).sum()) > 0
+
+
+def test_invalid_arguments(plc):
+    with pytest.raises(plc.PlcError) as e:
+        plc.Context(10, 100.0)          # prime factor 5
+    assert e.value.status == 1
+    with pytest.raises(plc.PlcError):
+        plc.Context(7, 100.0)           # odd
+    c = plc.Context(8, 100.0)
+    x = c.field()
+    with pytest.raises(plc.PlcError):
+        c.prior_apply(x)                # no prior yet
+    k = np.array([0.1, 0.2, 0.3])
+    with pytest.raises(plc.PlcError):
+        c.set_prior(k, np.ones(3), 0.0)  # does not cover the grid
+    kk, P = pk_table_for(8, 100.0)
+    with pytest.raises(plc.PlcError):
+        c.set_prior(kk, -P, 0.0)         # negative power
+    with pytest.raises(plc.PlcError):
+        c.set_prior(kk[::-1].copy(), P, 0.0)   # not ascending
+    c.set_prior(kk, P, 0.0)
+    N = torch.zeros((8, 8, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(plc.PlcError):
+        c.logpost_grad(x, N, None, -1.0)       # nbar <= 0
