@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark: 256^3 Poisson-lognormal MAP solve on one GB300.
+
+A step is one whole MAP solve (every part of the hot path): from s = mu,
+Newton-Krylov iterations (FP64 gradient of Sec. 3.1.2 through the 3D FFT
+prior, FP32 Jacobi-preconditioned CG on the Hessian, step length of
+Eq. New5, Armijo line search) until ||g|| / ||g0|| < 1e-6, on the production
+workload: 256^3 cells, 500 Mpc/h box, sigma_G = 1.8, nbar = 1, w = 1, a
+512-bin P(k) table; synthetic lognormal-Poisson counts (seed 1 + rank).
+
+Printed as one JSON line.  `value` is MAP solves per second over all ranks
+(inputs resident in HBM); `e2e` the same with the counts copied in from
+pinned host memory and the MAP copied out inside each step.  Extra keys:
+time-to-MAP of the mixed and the FP64 forms, Hessian-vector products per
+second (FP32, FP64), per-kernel device time and the roofline of the
+dominant kernel, and the FP64 CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl plc|reference]
+
+With --impl reference the FP64 CPU oracle is timed instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("256³ time-to-MAP (‖g‖/‖g0‖<1e-6) & Hv/s; mixed vs FP64 GPU, "
+          "HBM frac")
+UNIT = "MAP/s"
+WORKLOAD = "production256"
+TOL = 1e-6
+# Hessian-vector products and gradients of one Newton-Krylov MAP solve on this
+# workload in FP64 (the oracle's precision), used to scale the oracle's timed
+# sample (one Hv and one gradient) to MAP/s.  Same iteration as the oracle.
+REF_HV_PER_MAP = None      # filled from the FP64 GPU solve when both arms run
+REF_GRAD_PER_MAP = None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel kind inside the mixed MAP solve
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(n: int) -> dict:
+    n3, h = n ** 3, n // 2 + 1
+    spec32, spec64 = 8 * h * n * n, 16 * h * n * n
+    return {
+        # FP32 Hessian-vector product of the CG: p <- M^-1 r + beta p fused in
+        "xf_f32": 4 * n3 * 4 + spec32,          # read r, D, p; write p; write spectrum
+        "yf_f32": 2 * spec32, "z_f32": 2 * spec32, "yi_f32": 2 * spec32,
+        "xi_f32": spec32 + 3 * 4 * n3,          # read spectrum, D, p; write Hp
+        # FP64 gradient with the Newton step fused in
+        "xf_f64": (8 + 4 + 8) * n3 + spec64,    # read s, xi; write s; write spectrum
+        "yf_f64": 2 * spec64, "z_f64": 2 * spec64, "yi_f64": 2 * spec64,
+        "xi_f64": spec64 + (8 + 4 + 8 + 8 + 4) * n3,   # read spectrum, s, N; write g, D, D32
+        "cg_update": 7 * 4 * n3,                # read x, p, r, Hp, D; write x, r
+        "cg_init": (8 + 4 + 4 + 4) * n3,        # read g, D; write r, x
+        "dirstats": (4 + 8 + 4 + 8 + 4) * n3,   # xi, g, r, D, N
+        "trial": (4 + 8) * n3,                  # xi, D
+    }
+
+
+def fft_flops(n: int) -> float:
+    """5 N log2 N per complex line transform of length n."""
+    return 5.0 * n * math.log2(n)
+
+
+def algorithmic_flops_f64(n: int) -> dict:
+    h = n // 2 + 1
+    lines_x, lines_yz = n * n / 2, h * n
+    return {"xf_f64": lines_x * fft_flops(n), "yf_f64": lines_yz * fft_flops(n),
+            "z_f64": 2 * lines_yz * fft_flops(n), "yi_f64": lines_yz * fft_flops(n),
+            "xi_f64": lines_x * fft_flops(n)}
+
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (no FP64 figure is measured)
+
+
+def load_traffic(n: int):
+    """Per-launch DRAM bytes from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{WORKLOAD}.txt")
+    if not os.path.exists(path):
+        return {}, None
+    from paper_0911_1407_gb300 import build
+    src_hash = build.source_hash()
+    out, file_hash = {}, None
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("# csrc "):
+            file_hash = line.split()[2]
+        elif line and not line.startswith("#"):
+            k, v = line.split()[:2]
+            out[k] = float(v)
+    return (out, file_hash) if file_hash == src_hash else ({}, file_hash)
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores
+# ----------------------------------------------------------------------------
+def time_oracle_sample(m, repeats: int = 1):
+    """One oracle Hessian-vector product and one gradient at full size."""
+    from oracle import plc as orc
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab)
+    s = np.full(m.N.shape, m.mu) + 0.1 * np.random.default_rng(0).standard_normal(m.N.shape)
+    v = np.random.default_rng(1).standard_normal(m.N.shape)
+    t_hv, t_g = [], []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        orc.hessvec(s, v, p)
+        t1 = time.perf_counter()
+        orc.gradient(s, p)
+        orc.neg_log_posterior(s, p)
+        t2 = time.perf_counter()
+        t_hv.append(t1 - t0)
+        t_g.append(t2 - t1)
+    return min(t_hv), min(t_g)
+
+
+def reference_arm(args):
+    from paper_0911_1407_gb300 import mocks
+    m = mocks.make_mock(mocks.WORKLOADS[WORKLOAD])
+    hv_per_map = REF_HV_PER_MAP or 200
+    grad_per_map = REF_GRAD_PER_MAP or 15
+    for _ in range(args.warmup):
+        time_oracle_sample(m)
+    times = []
+    for _ in range(args.steps):
+        t_hv, t_g = time_oracle_sample(m)
+        times.append(t_hv * hv_per_map + t_g * grad_per_map)
+    t_map = statistics.median(times)
+    cores = os.cpu_count()
+    sample = (f"one FP64 oracle Hessian-vector product and one gradient+objective at 256^3 per step, "
+              f"scaled to one MAP by {hv_per_map} Hv and {grad_per_map} gradients per solve")
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t_map, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_map, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": 256, "box": 500.0, "sigma_G": 1.8, "nbar": 1.0},
+            "cpu_baseline": {"value": 1.0 / t_map, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": 1.0 / t_map, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["plc", "reference"], default="plc")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 solve, Hv/s sweeps and the CPU baseline")
+    args = ap.parse_args(argv)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return 0
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_0911_1407_gb300 import build
+    build.build()
+    import paper_0911_1407_gb300 as plc
+    from paper_0911_1407_gb300 import mocks
+
+    spec = mocks.replace(mocks.WORKLOADS[WORKLOAD], seed=1 + rank, mock_id=rank)
+    m = mocks.make_mock(spec)
+    n = m.n
+    stream = torch.cuda.current_stream()
+    ctx = plc.Context(n, m.box, "mixed")
+    ctx.set_prior(m.k_tab, m.P_tab, m.mu)
+    N_dev = torch.from_numpy(m.N).cuda()
+    s = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+
+    def step():
+        s.fill_(m.mu)
+        return ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K whole MAP solves -----------------------
+    clocks = ClockSampler(local)
+    ctx.profile_enable(True)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step().stats for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    if world > 1:
+        t = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = world * args.steps / t_dev
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # ---------------- end to end: host buffers in and out --------------------
+    N_host = torch.from_numpy(m.N).pin_memory()
+    s_host = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+    def e2e_step():
+        N_dev.copy_(N_host, non_blocking=True)
+        step()
+        s_host.copy_(s, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- per-kernel roofline (dominant kernel) ------------------
+    hbm_peak, peak_kind = peaks()
+    abytes = algorithmic_bytes(n)
+    aflops = algorithmic_flops_f64(n)
+    total_ms = sum(v[2] for v in prof.values())
+    kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[2] / v[1] if v[1] else None,
+                   "share": v[2] / total_ms if total_ms else None}
+               for k, v in prof.items() if v[0]}
+    dom = max(prof, key=lambda k: prof[k][2])
+    avg_s = prof[dom][2] / prof[dom][1] / 1e3
+    traffic, _ = load_traffic(n)
+    if dom.endswith("f64") and dom in aflops:
+        ach = aflops[dom] / avg_s / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "traffic": traffic.get(dom), "peak_kind": "nominal FP64"}
+    else:
+        ach = abytes[dom] / avg_s / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic.get(dom),
+                    "peak_kind": peak_kind}
+    hbm_kernels = {}
+    for k in prof:
+        if prof[k][1] and k in abytes and not k.endswith("f64"):
+            gbs = abytes[k] / (prof[k][2] / prof[k][1] / 1e3) / 1e9
+            hbm_kernels[k] = round(gbs / hbm_peak, 3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "box": m.box, "sigma_G": spec.sigma_G,
+                   "nbar": m.nbar, "w": 1, "pk_bins": spec.nbins, "tol": TOL,
+                   "precision": "mixed (FP32 FFT/CG, FP64 gradient, reductions, state)",
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (>1 GB touched per solve)"},
+        "clocks": clk,
+        "e2e": {"value": world * args.steps / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(N_host.numel() * 4),
+                "d2h_bytes_per_step": int(s_host.numel() * 8)},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "hbm_frac_fp32_kernels": hbm_kernels,
+        "kernels": kernels,
+        "solve": {"newton_iters": stats[-1]["newton_iters"], "cg_iters": stats[-1]["cg_iters"],
+                  "grad_evals": stats[-1]["grad_evals"], "grad_rel": stats[-1]["grad_rel"]},
+    }
+
+    if not args.no_extras:
+        extras(plc, m, ctx, s, N_dev, line, args)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(plc, m, ctx, s_mixed, N_dev, line, args):
+    """FP64 time-to-MAP, Hv/s in both precisions, accuracy, CPU oracle."""
+    import torch
+    n = m.n
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    # Hessian-vector products per second through plc_hessvec
+    for prec, reps in (("mixed", 200), ("fp64", 20)):
+        c = ctx if prec == "mixed" else plc.Context(n, m.box, "fp64")
+        if prec == "fp64":
+            c.set_prior(m.k_tab, m.P_tab, m.mu)
+        sv = s_mixed.to(c.real)
+        v = torch.randn((n, n, n), dtype=c.real, device="cuda")
+        hv = torch.empty_like(v)
+        for _ in range(3):
+            c.hessvec(sv, None, m.nbar, v, hv)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            c.hessvec(sv, None, m.nbar, v, hv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[prec] = reps / (e0.elapsed_time(e1) / 1e3)
+        if prec == "fp64":
+            ctx64 = c
+    hv_bytes = 12 * 4 * n ** 3
+    line["hv_per_s"] = {"f32": out["mixed"], "f64": out["fp64"],
+                        "f32_hbm_frac_12bn3_model": out["mixed"] * hv_bytes / 1e9 / peaks()[0]}
+    # FP64 time-to-MAP, and accuracy of the mixed MAP against it
+    s64 = torch.full((n, n, n), m.mu, dtype=torch.float64, device="cuda")
+    r = ctx64.newton_krylov_map(N_dev, None, m.nbar, s=s64, tol=TOL)    # warm-up
+    s64.fill_(m.mu)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r = ctx64.newton_krylov_map(N_dev, None, m.nbar, s=s64, tol=TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    d = (s_mixed - s64)
+    line["time_to_map_s"] = {"mixed": line["ms_per_step"] / 1e3, "fp64": t64}
+    line["fp64_solve"] = {"newton_iters": r.stats["newton_iters"], "cg_iters": r.stats["cg_iters"],
+                          "grad_evals": r.stats["grad_evals"], "grad_rel": r.stats["grad_rel"]}
+    line["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()),
+                             "rel_l2": float(d.norm() / s64.norm())}
+    # the FP64 oracle on the host cores, on a bounded sample
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        t_hv, t_g = time_oracle_sample(m)
+        hvc, gc = r.stats["hv_count"], r.stats["grad_evals"]
+        t_map = t_hv * hvc + t_g * gc
+        line["cpu_baseline"] = {
+            "value": 1.0 / t_map, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one oracle Hv ({t_hv:.2f} s) and one gradient+objective ({t_g:.2f} s) at "
+                       f"256^3, scaled by the FP64 solve's {hvc} Hv and {gc} gradients per MAP"),
+            "hv_per_s": 1.0 / t_hv}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -147,6 +147,23 @@ plc_status plc_map_vjp(plc_ctx* ctx, const double* s_map, const void* w,
                        double nbar, const double* u, double* vjp_N,
                        double* vjp_lnA, const plc_opts* opts, plc_stats* stats);
 
+/* Per-kernel launch counters and device time (an aid to profiling; the
+ * paper has no counterpart).  Launch counts are always kept.  on != 0 also
+ * brackets every launch with a pair of CUDA events on the context's stream
+ * (a small host cost per launch).  Either call resets the counters. */
+typedef struct {
+  char name[24];        /* kernel kind, e.g. "z_f32" (pass Z, FP32) */
+  long long launches;   /* launches since the last reset */
+  long long timed;      /* launches timed with events */
+  double total_ms;      /* summed event time of the timed launches */
+} plc_kernel_time;
+
+plc_status plc_profile_enable(plc_ctx* ctx, int on);
+
+/* Copy up to cap records into out (cap may be 0 to query *count, the number
+ * of kernel kinds).  Synchronises the stream. */
+plc_status plc_profile_read(plc_ctx* ctx, plc_kernel_time* out, int cap, int* count);
+
 /* Message of the last failure on this context ("" if none). */
 const char* plc_last_error(const plc_ctx* ctx);
 

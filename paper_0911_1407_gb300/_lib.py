@@ -25,7 +25,7 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
-           "plc_last_error", "plc_status_string"]
+           "plc_profile_enable", "plc_profile_read", "plc_last_error", "plc_status_string"]
 
 
 class PlcError(RuntimeError):
@@ -51,6 +51,11 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
+                ("timed", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
 _LIB: Optional[ctypes.CDLL] = None
 
 
@@ -74,6 +79,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_default_opts": (I, [ctypes.POINTER(Opts)]),
         "plc_newton_krylov_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_profile_enable": (I, [P, I]),
+        "plc_profile_read": (I, [P, ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]),
         "plc_last_error": (ctypes.c_char_p, [P]),
         "plc_status_string": (ctypes.c_char_p, [I]),
     }
@@ -205,6 +212,18 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return MapResult(s, st, stt.as_dict())
+
+    def profile_enable(self, timing: bool = True):
+        """Reset the per-kernel counters; timing=True also times every launch."""
+        self._check(self.lib.plc_profile_enable(self._h, int(bool(timing))))
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (launches, timed launches, total ms)} since the last reset."""
+        cnt = ctypes.c_int()
+        self._check(self.lib.plc_profile_read(self._h, None, 0, ctypes.byref(cnt)))
+        arr = (KernelTime * cnt.value)()
+        self._check(self.lib.plc_profile_read(self._h, arr, cnt.value, ctypes.byref(cnt)))
+        return {r.name.decode(): (r.launches, r.timed, r.total_ms) for r in arr}
 
     def map_vjp(self, s_map, w, nbar: float, u, raise_on_fail: bool = True, **opts):
         vjp_N = self.field(torch.float64)

@@ -40,6 +40,18 @@ def _newest_header() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
+def source_hash() -> str:
+    """Hash of every CUDA source and header: identifies the kernels' version."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(CSRC, "*"))) + [os.path.join(ROOT, "include", "plc.h")]
+    for f in files:
+        if os.path.isfile(f):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _compile(src: str, obj: str, verbose: bool, extra) -> str:
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     if verbose:

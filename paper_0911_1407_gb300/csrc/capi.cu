@@ -65,6 +65,7 @@ template <typename T> void dalloc(T** p, size_t bytes) {
 }
 
 void release(plc_ctx* c) {
+  plc::profile_release(c);
   void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->M64, c->M32, c->lk, c->lP,
                   c->sc, c->partials, c->f_g, c->f_D, c->f_D32, c->f_r, c->f_x, c->f_p, c->f_Hp};
   for (void* p : ptrs)
@@ -381,6 +382,31 @@ plc_status plc_map_vjp(plc_ctx* c, const double* s_map, const void* w, double nb
     if (st != PLC_OK) fail(c, st, "adjoint CG did not reach the tolerance");
     else c->err.clear();
     return st;
+  });
+}
+
+plc_status plc_profile_enable(plc_ctx* c, int on) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  return guarded(c, [&]() -> plc_status {
+    plc::profile_reset(c, on != 0);
+    return PLC_OK;
+  });
+}
+
+plc_status plc_profile_read(plc_ctx* c, plc_kernel_time* out, int cap, int* count) {
+  if (!c || !count || (cap > 0 && !out)) return fail(c, PLC_ERR_INVALID_ARG, "bad profile_read arguments");
+  return guarded(c, [&]() -> plc_status {
+    plc::check(cudaStreamSynchronize(c->stream), "stream synchronize");
+    plc::profile_collect(c);
+    *count = plc::S_NSITES;
+    for (int i = 0; i < plc::S_NSITES && i < cap; ++i) {
+      std::memset(out[i].name, 0, sizeof(out[i].name));
+      std::strncpy(out[i].name, plc::kSiteNames[i], sizeof(out[i].name) - 1);
+      out[i].launches = c->prof.launches[i];
+      out[i].timed = c->prof.timed[i];
+      out[i].total_ms = c->prof.ms[i];
+    }
+    return PLC_OK;
   });
 }
 

@@ -5,9 +5,34 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/plc.h"
 #include "common.cuh"
+
+namespace plc {
+
+// Launch sites of the library's kernels, for the counters and the optional
+// CUDA-event timing.
+enum Site {
+  S_XF64, S_YF64, S_Z64, S_YI64, S_XI64,
+  S_XF32, S_YF32, S_Z32, S_YI32, S_XI32,
+  S_CG_INIT, S_CG_UPDATE, S_DIRSTATS, S_TRIAL, S_DIAG, S_CONVERT, S_SETUP,
+  S_NSITES
+};
+extern const char* const kSiteNames[S_NSITES];
+
+struct Profiler {
+  bool timing = false;
+  long long launches[S_NSITES] = {};
+  long long timed[S_NSITES] = {};
+  double ms[S_NSITES] = {};
+  std::vector<cudaEvent_t> ev;      // 2 per slot
+  std::vector<int> site_of;         // site of each pending slot
+  int used = 0;
+};
+
+}  // namespace plc
 
 struct plc_ctx {
   int n = 0;
@@ -50,6 +75,7 @@ struct plc_ctx {
   void* f_p = nullptr;
   void* f_Hp = nullptr;
 
+  plc::Profiler prof;
   std::string err;
 
   size_t n3() const { return (size_t)n * n * n; }
@@ -88,6 +114,19 @@ template <typename TC, typename TG> void dirstats(plc_ctx* c, const TC* xi, cons
 template <typename TC, typename TG> void trial(plc_ctx* c, const TC* xi, const TG* D, double tau);
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D);
 template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* dst);
+
+// Counts a launch and, when timing is on, brackets it with CUDA events.
+class LaunchScope {
+ public:
+  LaunchScope(plc_ctx* c, Site site);
+  ~LaunchScope();
+ private:
+  plc_ctx* c_;
+  int slot_;
+};
+void profile_collect(plc_ctx* c);   // synchronises and accumulates pending timings
+void profile_reset(plc_ctx* c, bool timing);
+void profile_release(plc_ctx* c);
 
 void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int nk);
 void reset_ticket(plc_ctx* c);

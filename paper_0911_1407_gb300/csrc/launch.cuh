@@ -34,16 +34,32 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
   cpx<T>* B = static_cast<cpx<T>*>(c->specB);
   const cpx<T>* tw = twiddles<T>(c);
   const dim3 gx((n + G::RY - 1) / G::RY, n), gy((n + G::L - 1) / G::L, h);
+  const int s0 = sizeof(T) == 8 ? S_XF64 : S_XF32;
   set_smem(k_xf<T, Pro>, sm);
-  k_xf<T, Pro><<<gx, kThreads, sm, c->stream>>>(pro, A, c->plan, tw, done);
   set_smem(k_yf<T>, sm);
-  k_yf<T><<<gy, kThreads, sm, c->stream>>>(A, B, c->plan, tw, done);
   set_smem(k_z<T>, sm);
-  k_z<T><<<gy, kThreads, sm, c->stream>>>(B, multiplier<T>(c), zero_dc, c->plan, tw, done);
   set_smem(k_yi<T>, sm);
-  k_yi<T><<<gy, kThreads, sm, c->stream>>>(B, A, c->plan, tw, done);
   set_smem(k_xi<T, Epi, Fin>, sm);
-  k_xi<T, Epi, Fin><<<gx, kThreads, sm, c->stream>>>(A, epi, fin, red_args(c), c->plan, tw, done);
+  {
+    LaunchScope ls(c, Site(s0 + 0));
+    k_xf<T, Pro><<<gx, kThreads, sm, c->stream>>>(pro, A, c->plan, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 1));
+    k_yf<T><<<gy, kThreads, sm, c->stream>>>(A, B, c->plan, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 2));
+    k_z<T><<<gy, kThreads, sm, c->stream>>>(B, multiplier<T>(c), zero_dc, c->plan, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 3));
+    k_yi<T><<<gy, kThreads, sm, c->stream>>>(B, A, c->plan, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 4));
+    k_xi<T, Epi, Fin><<<gx, kThreads, sm, c->stream>>>(A, epi, fin, red_args(c), c->plan, tw, done);
+  }
   check(cudaGetLastError(), "spectral pipeline launch");
 }
 
@@ -90,6 +106,7 @@ template <typename TC, typename TB> void cg_init(plc_ctx* c, const TB* b, bool n
                                                  const TC* D, TC* r, TC* x, double rtol2,
                                                  int max_iter, bool jac) {
   const int nb = pw_blocks(c);
+  LaunchScope ls(c, S_CG_INIT);
   if (jac)
     k_cg_init<TC, TB, true><<<nb, kThreads, 0, c->stream>>>(b, negate, D, (TC)c->jac_c, r, x,
                                                              c->n3(), red_args(c), rtol2, max_iter);
@@ -102,6 +119,7 @@ template <typename TC, typename TB> void cg_init(plc_ctx* c, const TB* b, bool n
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
                                       const TC* D, bool jac) {
   const int nb = pw_blocks(c);
+  LaunchScope ls(c, S_CG_UPDATE);
   if (jac)
     k_cg_update<TC, true><<<nb, kThreads, 0, c->stream>>>(x, r, p, Hp, D, (TC)c->jac_c, c->n3(),
                                                            red_args(c));
@@ -113,22 +131,26 @@ template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, con
 
 template <typename TC, typename TG> void dirstats(plc_ctx* c, const TC* xi, const TG* g,
                                                   const TC* r, const TG* D, const int32_t* N) {
+  LaunchScope ls(c, S_DIRSTATS);
   k_dirstats<TC, TG><<<pw_blocks(c), kThreads, 0, c->stream>>>(xi, g, r, D, N, c->n3(),
                                                                 red_args(c));
   check(cudaGetLastError(), "k_dirstats");
 }
 
 template <typename TC, typename TG> void trial(plc_ctx* c, const TC* xi, const TG* D, double tau) {
+  LaunchScope ls(c, S_TRIAL);
   k_trial<TC, TG><<<pw_blocks(c), kThreads, 0, c->stream>>>(xi, D, tau, c->n3(), red_args(c));
   check(cudaGetLastError(), "k_trial");
 }
 
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D) {
+  LaunchScope ls(c, S_DIAG);
   k_diag<TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(s, w, nbar, D, c->n3());
   check(cudaGetLastError(), "k_diag");
 }
 
 template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* dst) {
+  LaunchScope ls(c, S_CONVERT);
   k_convert<TD, TS><<<pw_blocks(c), kThreads, 0, c->stream>>>(src, dst, c->n3());
   check(cudaGetLastError(), "k_convert");
 }

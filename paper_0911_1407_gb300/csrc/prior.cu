@@ -48,6 +48,57 @@ k_jacobi_constant(const double* __restrict__ M64, int n, RedArgs ra) {
   block_reduce_finish<1, 0u>(acc, ra, FinStore<1>{});
 }
 
+const char* const kSiteNames[S_NSITES] = {
+    "xf_f64", "yf_f64", "z_f64", "yi_f64", "xi_f64",
+    "xf_f32", "yf_f32", "z_f32", "yi_f32", "xi_f32",
+    "cg_init", "cg_update", "dirstats", "trial", "diag", "convert", "setup"};
+
+constexpr int kProfSlots = 512;
+
+LaunchScope::LaunchScope(plc_ctx* c, Site site) : c_(c), slot_(-1) {
+  Profiler& p = c->prof;
+  p.launches[site]++;
+  if (!p.timing) return;
+  if (p.ev.empty()) {
+    p.ev.resize(2 * kProfSlots);
+    for (auto& e : p.ev) check(cudaEventCreate(&e), "cudaEventCreate");
+    p.site_of.assign(kProfSlots, 0);
+  }
+  if (p.used == kProfSlots) profile_collect(c);
+  slot_ = p.used++;
+  p.site_of[slot_] = site;
+  check(cudaEventRecord(p.ev[2 * slot_], c->stream), "cudaEventRecord");
+}
+
+LaunchScope::~LaunchScope() {
+  if (slot_ >= 0) cudaEventRecord(c_->prof.ev[2 * slot_ + 1], c_->stream);
+}
+
+void profile_collect(plc_ctx* c) {
+  Profiler& p = c->prof;
+  if (p.used == 0) return;
+  check(cudaEventSynchronize(p.ev[2 * (p.used - 1) + 1]), "cudaEventSynchronize");
+  for (int i = 0; i < p.used; ++i) {
+    float ms = 0.f;
+    check(cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]), "cudaEventElapsedTime");
+    p.ms[p.site_of[i]] += ms;
+    p.timed[p.site_of[i]] += 1;
+  }
+  p.used = 0;
+}
+
+void profile_reset(plc_ctx* c, bool timing) {
+  Profiler& p = c->prof;
+  if (p.used) profile_collect(c);
+  for (int i = 0; i < S_NSITES; ++i) { p.launches[i] = 0; p.timed[i] = 0; p.ms[i] = 0.0; }
+  p.timing = timing;
+}
+
+void profile_release(plc_ctx* c) {
+  for (auto& e : c->prof.ev) cudaEventDestroy(e);
+  c->prof.ev.clear();
+}
+
 void check(cudaError_t e, const char* where) {
   if (e != cudaSuccess) throw CudaError{e, where};
 }
@@ -68,10 +119,12 @@ void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int n
   check(cudaMemcpyAsync(c->lP, lP_host, sizeof(double) * nk, cudaMemcpyHostToDevice, c->stream),
         "copy ln P");
   const int nb = (c->nm2 + kThreads - 1) / kThreads;
+  LaunchScope ls(c, S_SETUP);
   k_build_multiplier<<<nb, kThreads, 0, c->stream>>>(c->M64, c->M32, c->nm2, c->n, c->box, c->lk,
                                                       c->lP, nk, c->inv_dc);
   check(cudaGetLastError(), "k_build_multiplier");
   reset_ticket(c);
+  LaunchScope ls2(c, S_SETUP);
   k_jacobi_constant<<<pw_blocks(c), kThreads, 0, c->stream>>>(c->M64, c->n, red_args(c));
   check(cudaGetLastError(), "k_jacobi_constant");
   read_scalars(c);
