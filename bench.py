@@ -224,7 +224,13 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["plc", "reference"], default="plc")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 solve, Hv/s sweeps and the CPU baseline")
+    ap.add_argument("--micro", choices=["hv32", "hv64", "grad32", "grad64"],
+                    help="profiling aid: run --reps single operator calls at size --n and exit")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
+    if args.micro:
+        return micro(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -371,6 +377,39 @@ def main(argv=None):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def micro(args):
+    """A few calls of one operator on a small synthetic field (for ncu)."""
+    import torch
+    from paper_0911_1407_gb300 import build
+    build.build()
+    import paper_0911_1407_gb300 as plc
+    from paper_0911_1407_gb300 import mocks
+    n, box = args.n, 500.0 * args.n / 256
+    A = mocks.amplitude_for_sigma(n, box, 1.8)
+    k, P = mocks.pk_table(n, box, A)
+    prec = "fp64" if args.micro.endswith("64") else "mixed"
+    c = plc.Context(n, box, prec)
+    c.set_prior(k, P, -1.62)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    s = (-1.62 + 0.5 * torch.randn((n,) * 3, generator=g, device="cuda", dtype=torch.float64)).to(c.real)
+    v = torch.randn((n,) * 3, generator=g, device="cuda", dtype=torch.float64).to(c.real)
+    N = torch.poisson(torch.exp(s.double())).to(torch.int32)
+    out = torch.empty_like(v)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        if args.micro.startswith("hv"):
+            c.hessvec(s, None, 1.0, v, out)
+        else:
+            c.logpost_grad(s, N, None, 1.0, grad=out)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"micro": args.micro, "n": n, "reps": args.reps,
+                      "ms_per_call": e0.elapsed_time(e1) / args.reps}))
     return 0
 
 
