@@ -164,6 +164,31 @@ plc_status plc_profile_enable(plc_ctx* ctx, int on);
  * of kernel kinds).  Synchronises the stream. */
 plc_status plc_profile_read(plc_ctx* ctx, plc_kernel_time* out, int cap, int* count);
 
+/* Hessian-vector product that allocates no device memory (the paper has no
+ * counterpart; this is a service for callers that cannot call cudaMalloc --
+ * programs whose device memory is reserved up front by an allocator they do
+ * not own, real-time or certified code that forbids allocation after
+ * start-up, plug-ins that may not create allocations of their own).
+ * Computes the same Hv = S^-1 v + nbar w e^s v as plc_hessvec on a PLC_FP64
+ * context, without a context: the prior is given by HOST arrays k, P
+ * (plc_set_prior's rules, 2 <= nk <= 1024) and inv_lambda_dc; s, w (NULL =
+ * 1), v, Hv are double DEVICE fields of n^3 cells, 16-byte aligned.
+ * Limit: n <= 64 (even, prime factors 2 and 3); larger n returns
+ * PLC_ERR_INVALID_ARG with a message in plc_last_error(NULL).
+ * Scratch: one file-scope device array of about 4.2 MiB that every GPU
+ * which loads the library holds until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents (each call rewrites everything it reads, so nothing needs
+ * clearing); two calls whose work overlaps on the same GPU, e.g. from
+ * different streams, race on it: serialise them.  Enqueued on cuda_stream
+ * (NULL = legacy default stream); returns after enqueue. */
+plc_status plc_hessvec_noalloc(int n, double box, const double* k, const double* P,
+                               int nk, double inv_lambda_dc, const double* s,
+                               const double* w, double nbar, const double* v,
+                               double* Hv, void* cuda_stream);
+
 /* Message of the last failure on this context ("" if none). */
 const char* plc_last_error(const plc_ctx* ctx);
 

@@ -25,7 +25,8 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
-           "plc_profile_enable", "plc_profile_read", "plc_last_error", "plc_status_string"]
+           "plc_profile_enable", "plc_profile_read", "plc_hessvec_noalloc", "plc_last_error",
+           "plc_status_string"]
 
 
 class PlcError(RuntimeError):
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_profile_enable": (I, [P, I]),
         "plc_profile_read": (I, [P, ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]),
+        "plc_hessvec_noalloc": (I, [I, D, DP, DP, I, D, P, P, D, P, P, P]),
         "plc_last_error": (ctypes.c_char_p, [P]),
         "plc_status_string": (ctypes.c_char_p, [I]),
     }
@@ -113,6 +115,28 @@ def _ptr(t: Optional[torch.Tensor], n: int, dtype, name: str, required: bool = T
     if tuple(t.shape) != (n, n, n) or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous ({n}, {n}, {n}) tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def hessvec_noalloc(n: int, box: float, k, P, inv_lambda_dc: float, s: torch.Tensor,
+                    w: Optional[torch.Tensor], nbar: float, v: torch.Tensor, out: torch.Tensor,
+                    stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """plc_hessvec_noalloc: FP64 H v for n <= 64 using the library's static
+    scratch (for callers that cannot allocate device memory).  `out` must be
+    supplied by the caller."""
+    lib = load()
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    DP = ctypes.POINTER(ctypes.c_double)
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    st = lib.plc_hessvec_noalloc(int(n), float(box), k.ctypes.data_as(DP), P.ctypes.data_as(DP),
+                                 int(k.size), float(inv_lambda_dc),
+                                 _ptr(s, n, torch.float64, "s"), _ptr(w, n, torch.float64, "w", False),
+                                 float(nbar), _ptr(v, n, torch.float64, "v"),
+                                 _ptr(out, n, torch.float64, "out"),
+                                 ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise PlcError(st, lib.plc_last_error(None).decode())
+    return out
 
 
 @dataclass

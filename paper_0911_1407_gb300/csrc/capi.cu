@@ -132,6 +132,11 @@ plc_status check_opts(plc_ctx* c, const plc_opts& o) {
 
 }  // namespace
 
+namespace plc {
+// Records a failure that has no context (read back by plc_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace plc
+
 extern "C" {
 
 const char* plc_status_string(int s) {
