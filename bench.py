@@ -112,21 +112,22 @@ class ClockSampler:
 # algorithmic bytes per launch of each kernel kind inside the mixed MAP solve
 # ----------------------------------------------------------------------------
 def algorithmic_bytes(n: int) -> dict:
+    """Bytes each kernel kind must move per launch in the mixed MAP solve."""
     n3, h = n ** 3, n // 2 + 1
     spec32, spec64 = 8 * h * n * n, 16 * h * n * n
     return {
-        # FP32 Hessian-vector product of the CG: p <- M^-1 r + beta p fused in
-        "xf_f32": 4 * n3 * 4 + spec32,          # read r, D, p; write p; write spectrum
+        # FP32 Hessian-vector product of the CG, direction update fused in
+        "xf_f32": 4 * 4 * n3 + spec32,          # read r, D, p; write p; write spectrum
         "yf_f32": 2 * spec32, "z_f32": 2 * spec32, "yi_f32": 2 * spec32,
         "xi_f32": spec32 + 3 * 4 * n3,          # read spectrum, D, p; write Hp
-        # FP64 gradient with the Newton step fused in
-        "xf_f64": (8 + 4 + 8) * n3 + spec64,    # read s, xi; write s; write spectrum
-        "yf_f64": 2 * spec64, "z_f64": 2 * spec64, "yi_f64": 2 * spec64,
-        "xi_f64": spec64 + (8 + 4 + 8 + 8 + 4) * n3,   # read spectrum, s, N; write g, D, D32
+        # gradients with the Newton step fused in (FP32 first phase, FP64 last)
+        "grad_xf_f32": (8 + 4 + 8) * n3 + spec32,   # read s, xi; write s; write spectrum
+        "grad_yf_f32": 2 * spec32, "grad_z_f32": 2 * spec32, "grad_yi_f32": 2 * spec32,
+        "grad_xi_f32": spec32 + (8 + 4 + 4 + 4) * n3,   # read spectrum, s, N; write D, r
+        "grad_xf_f64": (8 + 4 + 8) * n3 + spec64,
+        "grad_yf_f64": 2 * spec64, "grad_z_f64": 2 * spec64, "grad_yi_f64": 2 * spec64,
+        "grad_xi_f64": spec64 + (8 + 4 + 4 + 4) * n3,
         "cg_update": 7 * 4 * n3,                # read x, p, r, Hp, D; write x, r
-        "cg_init": (8 + 4 + 4 + 4) * n3,        # read g, D; write r, x
-        "dirstats": (4 + 8 + 4 + 8 + 4) * n3,   # xi, g, r, D, N
-        "trial": (4 + 8) * n3,                  # xi, D
     }
 
 
@@ -138,9 +139,11 @@ def fft_flops(n: int) -> float:
 def algorithmic_flops_f64(n: int) -> dict:
     h = n // 2 + 1
     lines_x, lines_yz = n * n / 2, h * n
-    return {"xf_f64": lines_x * fft_flops(n), "yf_f64": lines_yz * fft_flops(n),
-            "z_f64": 2 * lines_yz * fft_flops(n), "yi_f64": lines_yz * fft_flops(n),
-            "xi_f64": lines_x * fft_flops(n)}
+    f = {"xf_f64": lines_x * fft_flops(n), "yf_f64": lines_yz * fft_flops(n),
+         "z_f64": 2 * lines_yz * fft_flops(n), "yi_f64": lines_yz * fft_flops(n),
+         "xi_f64": lines_x * fft_flops(n)}
+    f.update({"grad_" + k: v for k, v in list(f.items())})
+    return f
 
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 rate (no FP64 figure is measured)
@@ -367,8 +370,8 @@ def main(argv=None):
         "roofline": roofline,
         "hbm_frac_fp32_kernels": hbm_kernels,
         "kernels": kernels,
-        "solve": {"newton_iters": stats[-1]["newton_iters"], "cg_iters": stats[-1]["cg_iters"],
-                  "grad_evals": stats[-1]["grad_evals"], "grad_rel": stats[-1]["grad_rel"]},
+        "solve": {k: stats[-1][k] for k in ("newton_iters", "cg_iters", "grad_evals",
+                                             "grad_evals_fp64", "grad_rel")},
     }
 
     if not args.no_extras:
@@ -454,8 +457,8 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     t64 = e0.elapsed_time(e1) / 1e3
     d = (s_mixed - s64)
     line["time_to_map_s"] = {"mixed": line["ms_per_step"] / 1e3, "fp64": t64}
-    line["fp64_solve"] = {"newton_iters": r.stats["newton_iters"], "cg_iters": r.stats["cg_iters"],
-                          "grad_evals": r.stats["grad_evals"], "grad_rel": r.stats["grad_rel"]}
+    line["fp64_solve"] = {k: r.stats[k] for k in ("newton_iters", "cg_iters", "grad_evals",
+                                                  "grad_rel")}
     line["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()),
                              "rel_l2": float(d.norm() / s64.norm())}
     # the FP64 oracle on the host cores, on a bounded sample

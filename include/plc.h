@@ -107,13 +107,17 @@ typedef struct {
   double step_cap;     /* max |tau xi| per Newton step (default 2) */
   double eta_max;      /* CG forcing term cap (default 0.5) */
   int cg_chunk;        /* CG iterations enqueued between host checks (default 8) */
+  double mixed_switch; /* PLC_MIXED: gradients in FP32 while ||g|| / ||g0|| is at or
+                          above this, in FP64 below it (default 1e-3; >= 1 means FP64
+                          throughout).  The stopping test is always taken in FP64. */
 } plc_opts;
 
 typedef struct {
   int newton_iters;    /* outer iterations taken */
   int cg_iters;        /* total CG iterations */
   int hv_count;        /* Hessian-vector products applied */
-  int grad_evals;      /* gradient evaluations (FP64 in both modes) */
+  int grad_evals;      /* gradient evaluations, line-search trials included */
+  int grad_evals_fp64; /* of which evaluated with FP64 transforms */
   double grad_rel;     /* final ||g|| / ||g0|| */
   double g0_norm;      /* ||g0|| used */
   double neg_logpost;  /* final -ln P(s|N) (constants dropped) */
@@ -125,7 +129,7 @@ plc_status plc_default_opts(plc_opts* opts);
 
 /* MAP by inexact Newton-Krylov (Sec. 3.1): s <- s + tau xi with tau from
  * Eq. (New5), xi from preconditioned CG on H xi = -g, a step cap and an
- * Armijo backtracking line search.  s_inout (double, device) holds the start
+ * Armijo backtracking line search whose trials are gradient evaluations.  s_inout (double, device) holds the start
  * point on entry (e.g. filled with mu) and the MAP on exit.  N: int32 field;
  * w: double field or NULL (double in both precisions).  opts NULL = defaults;
  * stats may be NULL.  Returns PLC_ERR_NOT_CONVERGED with s_inout holding the

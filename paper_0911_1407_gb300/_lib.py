@@ -39,13 +39,13 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_cg", ctypes.c_int),
                 ("precond", ctypes.c_int), ("g0_norm", ctypes.c_double),
                 ("step_cap", ctypes.c_double), ("eta_max", ctypes.c_double),
-                ("cg_chunk", ctypes.c_int)]
+                ("cg_chunk", ctypes.c_int), ("mixed_switch", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("hv_count", ctypes.c_int), ("grad_evals", ctypes.c_int),
-                ("grad_rel", ctypes.c_double), ("g0_norm", ctypes.c_double),
+                ("grad_evals_fp64", ctypes.c_int), ("grad_rel", ctypes.c_double), ("g0_norm", ctypes.c_double),
                 ("neg_logpost", ctypes.c_double), ("ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:

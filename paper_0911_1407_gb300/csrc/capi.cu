@@ -127,6 +127,7 @@ plc_status check_opts(plc_ctx* c, const plc_opts& o) {
   if (!(o.step_cap > 0.0) || !(o.eta_max > 0.0) || o.eta_max >= 1.0 || o.g0_norm < 0.0)
     return fail(c, PLC_ERR_INVALID_ARG, "bad step_cap / eta_max / g0_norm");
   if (o.cg_chunk < 1) return fail(c, PLC_ERR_INVALID_ARG, "opts.cg_chunk must be >= 1");
+  if (!(o.mixed_switch >= 0.0)) return fail(c, PLC_ERR_INVALID_ARG, "opts.mixed_switch must be >= 0");
   return PLC_OK;
 }
 
@@ -164,6 +165,7 @@ plc_status plc_default_opts(plc_opts* o) {
   o->step_cap = 2.0;
   o->eta_max = 0.5;
   o->cg_chunk = 8;
+  o->mixed_switch = 1e-3;
   return PLC_OK;
 }
 
@@ -307,11 +309,11 @@ plc_status plc_logpost_grad(plc_ctx* c, const void* s, const int32_t* N, const v
   return guarded(c, [&]() -> plc_status {
     plc::reset_ticket(c);
     if (c->precision == PLC_FP64)
-      plc::grad<double>(c, static_cast<const double*>(s), static_cast<const double*>(w), N, nbar,
-                        static_cast<double*>(grad), nullptr, nullptr);
+      plc::grad_public<double>(c, static_cast<const double*>(s), static_cast<const double*>(w), N,
+                               nbar, static_cast<double*>(grad));
     else
-      plc::grad<float>(c, static_cast<const float*>(s), static_cast<const float*>(w), N, nbar,
-                       static_cast<float*>(grad), nullptr, nullptr);
+      plc::grad_public<float>(c, static_cast<const float*>(s), static_cast<const float*>(w), N,
+                              nbar, static_cast<float*>(grad));
     if (neg_logpost) {
       plc::read_scalars(c);
       const double* r = c->sc_host->red;

@@ -37,13 +37,14 @@ struct DevScalars {
   double rz;                 // r^T M^-1 r
   double alpha, beta;
   double rr;                 // ||r||^2
-  double bnorm2;             // ||b||^2
-  double rtol2;              // CG stops at ||r||^2 <= rtol2 * bnorm2
+  double bnorm2;             // ||b||^2 of the current CG solve
   double pHp;
-  int iter, max_iter;
+  double xb;                 // xi^T b accumulated over the CG steps
+  double xHx;                // xi^T H xi accumulated over the CG steps
+  double xmax;               // max |xi| after the last CG step
+  int iter;                  // CG iterations of the current solve
   int done, breakdown;
   unsigned ticket;           // last-block-done counter
-  int pad;
 };
 
 template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {
@@ -160,6 +161,36 @@ __device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan&
     Ns *= R;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Per-thread accumulators.  Element-wise terms are formed and summed in the
+// field precision: plain FP64 for double fields, Kahan-compensated FP32 for
+// float fields (about one FP32 rounding of relative error, and no FP64
+// arithmetic per element, which runs at a small fraction of the FP32 rate).
+// Across threads and blocks the sums continue in FP64.
+// ---------------------------------------------------------------------------
+struct AccD {
+  double v;
+  __device__ __forceinline__ void init(bool is_max) { v = is_max ? -INFINITY : 0.0; }
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void max(double x) { v = fmax(v, x); }
+  __device__ __forceinline__ double get() const { return v; }
+};
+struct AccK {
+  float s, c;
+  __device__ __forceinline__ void init(bool is_max) { s = is_max ? -INFINITY : 0.f; c = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ void max(float x) { s = fmaxf(s, x); }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+template <typename T> struct AccOf;
+template <> struct AccOf<double> { using type = AccD; };
+template <> struct AccOf<float> { using type = AccK; };
 
 // ---------------------------------------------------------------------------
 // Deterministic grid reduction.  Every block calls block_reduce_finish with

@@ -15,9 +15,13 @@ namespace plc {
 // Launch sites of the library's kernels, for the counters and the optional
 // CUDA-event timing.
 enum Site {
+  // pipelines of the CG Hessian-vector product (and the public operators)
   S_XF64, S_YF64, S_Z64, S_YI64, S_XI64,
   S_XF32, S_YF32, S_Z32, S_YI32, S_XI32,
-  S_CG_INIT, S_CG_UPDATE, S_DIRSTATS, S_TRIAL, S_DIAG, S_CONVERT, S_SETUP,
+  // pipelines of the Newton gradient (and line-search trials)
+  S_GXF64, S_GYF64, S_GZ64, S_GYI64, S_GXI64,
+  S_GXF32, S_GYF32, S_GZ32, S_GYI32, S_GXI32,
+  S_CG_INIT, S_CG_UPDATE, S_DIAG, S_CONVERT, S_SETUP,
   S_NSITES
 };
 extern const char* const kSiteNames[S_NSITES];
@@ -95,23 +99,22 @@ void check(cudaError_t e, const char* where);   // throws CudaError
 template <typename T> void prior_apply(plc_ctx* c, const T* x, T* y);
 template <typename T> void hessvec_s(plc_ctx* c, const T* s, const T* w, double nbar,
                                      const T* v, T* out);
-template <typename T> void grad(plc_ctx* c, const T* s, const T* w, const int32_t* N,
-                                double nbar, T* g, T* D, float* D32);
-template <typename T, typename TX> void grad_step(plc_ctx* c, T* s, const TX* xi, double tau,
-                                                  const T* w, const int32_t* N, double nbar,
-                                                  T* g, T* D, float* D32);
+// Public gradient: g (may be null) and the sums of -ln P (FP64).
+template <typename T> void grad_public(plc_ctx* c, const T* s, const T* w, const int32_t* N,
+                                       double nbar, T* g);
+// Newton gradient at s (after s += dtau xi when xi is not null), in transform
+// type T; writes D and r = -g in the CG type TC and starts the CG solve.
+template <typename T, typename TC> void grad_newton(plc_ctx* c, double* s, const TC* xi,
+                                                    double dtau, const double* w,
+                                                    const int32_t* N, double nbar, TC* D, TC* r,
+                                                    bool jac);
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac);
 template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL* lam);
 
 // Element-wise kernels.
-template <typename TC, typename TB> void cg_init(plc_ctx* c, const TB* b, bool negate,
-                                                 const TC* D, TC* r, TC* x, double rtol2,
-                                                 int max_iter, bool jac);
+template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC* r, bool jac);
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
-                                      const TC* D, bool jac);
-template <typename TC, typename TG> void dirstats(plc_ctx* c, const TC* xi, const TG* g,
-                                                  const TC* r, const TG* D, const int32_t* N);
-template <typename TC, typename TG> void trial(plc_ctx* c, const TC* xi, const TG* D, double tau);
+                                      const TC* D, bool jac, double rtol2, int max_iter);
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D);
 template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* dst);
 

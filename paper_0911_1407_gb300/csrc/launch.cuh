@@ -16,17 +16,20 @@ template <typename T> inline const T* multiplier(const plc_ctx* c);
 template <> inline const float* multiplier<float>(const plc_ctx* c) { return c->M32; }
 template <> inline const double* multiplier<double>(const plc_ctx* c) { return c->M64; }
 
-template <typename K> inline void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
-    check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
-          "cudaFuncSetAttribute");
+// Raise a kernel's dynamic shared-memory limit to what the largest grid
+// (n = 512) needs, once per kernel instantiation.
+template <typename T, typename K> inline void set_smem(K kernel) {
+  static const cudaError_t once = cudaFuncSetAttribute(
+      kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeom<T>::smem_bytes(512));
+  check(once, "cudaFuncSetAttribute");
 }
 
 inline RedArgs red_args(plc_ctx* c) { return RedArgs{c->partials, c->sc}; }
 
 // The five passes XF -> YF -> Z -> YI -> XI on the context's stream.
 template <typename T, typename Pro, typename Epi, typename Fin>
-void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done) {
+void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done,
+                  bool gradient_sites = false) {
   using G = PassGeom<T>;
   const int n = c->n, h = n / 2 + 1;
   const size_t sm = G::smem_bytes(n);
@@ -34,12 +37,13 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
   cpx<T>* B = static_cast<cpx<T>*>(c->specB);
   const cpx<T>* tw = twiddles<T>(c);
   const dim3 gx((n + G::RY - 1) / G::RY, n), gy((n + G::L - 1) / G::L, h);
-  const int s0 = sizeof(T) == 8 ? S_XF64 : S_XF32;
-  set_smem(k_xf<T, Pro>, sm);
-  set_smem(k_yf<T>, sm);
-  set_smem(k_z<T>, sm);
-  set_smem(k_yi<T>, sm);
-  set_smem(k_xi<T, Epi, Fin>, sm);
+  const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
+                                : (sizeof(T) == 8 ? S_XF64 : S_XF32);
+  set_smem<T>(k_xf<T, Pro>);
+  set_smem<T>(k_yf<T>);
+  set_smem<T>(k_z<T>);
+  set_smem<T>(k_yi<T>);
+  set_smem<T>(k_xi<T, Epi, Fin>);
   {
     LaunchScope ls(c, Site(s0 + 0));
     k_xf<T, Pro><<<gx, kThreads, sm, c->stream>>>(pro, A, c->plan, tw, done);
@@ -72,17 +76,23 @@ template <typename T> void hessvec_s(plc_ctx* c, const T* s, const T* w, double 
   run_pipeline<T>(c, ProLoad<T>{v}, EpiHessS<T>{s, w, (T)nbar, v, out}, FinNone{}, 0, nullptr);
 }
 
-template <typename T> void grad(plc_ctx* c, const T* s, const T* w, const int32_t* N,
-                                double nbar, T* g, T* D, float* D32) {
-  run_pipeline<T>(c, ProShift<T>{s, (T)c->mu},
-                  EpiGrad<T>{s, w, N, (T)nbar, (T)c->mu, g, D, D32}, FinStore<5>{}, 0, nullptr);
+template <typename T> void grad_public(plc_ctx* c, const T* s, const T* w, const int32_t* N,
+                                       double nbar, T* g) {
+  run_pipeline<T>(c, ProShift<T, T>{s, c->mu},
+                  EpiGrad<T, T, T>{s, w, N, nbar, c->mu, g, nullptr, nullptr, c->jac_c, 0},
+                  FinStore<6>{}, 0, nullptr, true);
 }
 
-template <typename T, typename TX> void grad_step(plc_ctx* c, T* s, const TX* xi, double tau,
-                                                  const T* w, const int32_t* N, double nbar,
-                                                  T* g, T* D, float* D32) {
-  run_pipeline<T>(c, ProStepShift<T, TX>{s, xi, tau, (T)c->mu},
-                  EpiGrad<T>{s, w, N, (T)nbar, (T)c->mu, g, D, D32}, FinStore<5>{}, 0, nullptr);
+template <typename T, typename TC> void grad_newton(plc_ctx* c, double* s, const TC* xi,
+                                                    double dtau, const double* w,
+                                                    const int32_t* N, double nbar, TC* D, TC* r,
+                                                    bool jac) {
+  const EpiGrad<T, double, TC> epi{s, w, N, nbar, c->mu, nullptr, D, r, c->jac_c, jac ? 1 : 0};
+  if (xi)
+    run_pipeline<T>(c, ProStepShift<T, double, TC>{s, xi, dtau, c->mu}, epi, FinGrad{}, 0,
+                    nullptr, true);
+  else
+    run_pipeline<T>(c, ProShift<T, double>{s, c->mu}, epi, FinGrad{}, 0, nullptr, true);
 }
 
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac) {
@@ -96,51 +106,35 @@ template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp
 }
 
 template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL* lam) {
-  run_pipeline<double>(c, ProShift<double>{s, c->mu}, EpiDot<double, TL>{lam}, FinStore<1>{},
-                       1, nullptr);
+  run_pipeline<double>(c, ProShift<double, double>{s, c->mu}, EpiDot<double, TL>{lam},
+                       FinStore<1>{}, 1, nullptr);
 }
 
 inline int pw_blocks(plc_ctx* c) { return pointwise_blocks((long long)c->n3(), c->sms); }
 
-template <typename TC, typename TB> void cg_init(plc_ctx* c, const TB* b, bool negate,
-                                                 const TC* D, TC* r, TC* x, double rtol2,
-                                                 int max_iter, bool jac) {
+template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC* r, bool jac) {
   const int nb = pw_blocks(c);
   LaunchScope ls(c, S_CG_INIT);
   if (jac)
-    k_cg_init<TC, TB, true><<<nb, kThreads, 0, c->stream>>>(b, negate, D, (TC)c->jac_c, r, x,
-                                                             c->n3(), red_args(c), rtol2, max_iter);
+    k_cg_init<TC, double, true><<<nb, kThreads, 0, c->stream>>>(b, D, (TC)c->jac_c, r, c->n3(),
+                                                                 red_args(c));
   else
-    k_cg_init<TC, TB, false><<<nb, kThreads, 0, c->stream>>>(b, negate, D, (TC)c->jac_c, r, x,
-                                                              c->n3(), red_args(c), rtol2, max_iter);
+    k_cg_init<TC, double, false><<<nb, kThreads, 0, c->stream>>>(b, D, (TC)c->jac_c, r, c->n3(),
+                                                                  red_args(c));
   check(cudaGetLastError(), "k_cg_init");
 }
 
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
-                                      const TC* D, bool jac) {
+                                      const TC* D, bool jac, double rtol2, int max_iter) {
   const int nb = pw_blocks(c);
   LaunchScope ls(c, S_CG_UPDATE);
   if (jac)
     k_cg_update<TC, true><<<nb, kThreads, 0, c->stream>>>(x, r, p, Hp, D, (TC)c->jac_c, c->n3(),
-                                                           red_args(c));
+                                                           red_args(c), rtol2, max_iter);
   else
     k_cg_update<TC, false><<<nb, kThreads, 0, c->stream>>>(x, r, p, Hp, D, (TC)c->jac_c, c->n3(),
-                                                            red_args(c));
+                                                            red_args(c), rtol2, max_iter);
   check(cudaGetLastError(), "k_cg_update");
-}
-
-template <typename TC, typename TG> void dirstats(plc_ctx* c, const TC* xi, const TG* g,
-                                                  const TC* r, const TG* D, const int32_t* N) {
-  LaunchScope ls(c, S_DIRSTATS);
-  k_dirstats<TC, TG><<<pw_blocks(c), kThreads, 0, c->stream>>>(xi, g, r, D, N, c->n3(),
-                                                                red_args(c));
-  check(cudaGetLastError(), "k_dirstats");
-}
-
-template <typename TC, typename TG> void trial(plc_ctx* c, const TC* xi, const TG* D, double tau) {
-  LaunchScope ls(c, S_TRIAL);
-  k_trial<TC, TG><<<pw_blocks(c), kThreads, 0, c->stream>>>(xi, D, tau, c->n3(), red_args(c));
-  check(cudaGetLastError(), "k_trial");
 }
 
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D) {

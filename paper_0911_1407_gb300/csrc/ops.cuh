@@ -4,8 +4,8 @@
 // epilogues (fused into the last pass) turn y = S^-1 x into the gradient or a
 // Hessian-vector product and accumulate the dot products the solver needs;
 // finalizers run once on the grid totals.  Element-wise kernels cover the CG
-// recurrences, the line-search sums and set-up work.  All reductions are in
-// FP64 whatever the field type.
+// recurrences and set-up work.  All reductions are in FP64 whatever the
+// field type.
 #pragma once
 
 #include "common.cuh"
@@ -18,27 +18,32 @@ template <typename T> struct ProLoad {
   __device__ T operator()(size_t i) const { return x[i]; }
 };
 
-// s - mu: the prior term of the gradient (Sec. 2.3, Eq. priorlog).
-template <typename T> struct ProShift {
-  const T* s;
-  T mu;
-  __device__ T operator()(size_t i) const { return s[i] - mu; }
+// s - mu: the prior term of the gradient (Sec. 2.3, Eq. priorlog).  s may be
+// held in a wider type than the transform.
+template <typename T, typename TS> struct ProShift {
+  const TS* s;
+  double mu;
+  // difference taken in the transform precision (no FP64 work for float)
+  __device__ T operator()(size_t i) const { return (T)s[i] - (T)mu; }
 };
 
-// Newton update s <- s + tau xi (Sec. 3.1), then s - mu for the new gradient.
-template <typename T, typename TX> struct ProStepShift {
-  T* s;
+// Newton update s <- s + dtau xi (Sec. 3.1), then s - mu for the gradient
+// at the new point.  Backtracking re-applies the difference of two step
+// lengths, so dtau may be negative.
+template <typename T, typename TS, typename TX> struct ProStepShift {
+  TS* s;
   const TX* xi;
-  double tau;
-  T mu;
+  double dtau;
+  double mu;
   __device__ T operator()(size_t i) const {
-    const T sn = (T)((double)s[i] + tau * (double)xi[i]);
+    const TS sn = s[i] + (TS)dtau * (TS)xi[i];
     s[i] = sn;
-    return sn - mu;
+    return (T)sn - (T)mu;
   }
 };
 
-// CG search direction p <- M^-1 r + beta p (beta from the device scalars).
+// CG search direction p <- M^-1 r + beta p (beta from the device scalars;
+// beta = 0 on the first step, where p is not read).
 template <typename T, bool JAC> struct ProCgDir {
   const T* r;
   const T* D;
@@ -48,7 +53,7 @@ template <typename T, bool JAC> struct ProCgDir {
   __device__ T operator()(size_t i) const {
     const T beta = (T)sc->beta;
     const T zi = JAC ? r[i] / (D[i] + c) : r[i];
-    const T pn = beta == (T)0 ? zi : zi + beta * p[i];   // first step: p = z
+    const T pn = beta == (T)0 ? zi : zi + beta * p[i];
     p[i] = pn;
     return pn;
   }
@@ -58,8 +63,9 @@ template <typename T, bool JAC> struct ProCgDir {
 template <typename T> struct EpiStore {
   static constexpr int NV = 0;
   static constexpr unsigned MAXMASK = 0;
+  using Acc = AccD;
   T* out;
-  __device__ void operator()(size_t i, T y, double*) const { out[i] = y; }
+  __device__ void operator()(size_t i, T y, Acc*) const { out[i] = y; }
 };
 
 // H v = S^-1 v + nbar w e^s v (Sec. 3.1.2) with the diagonal computed here.
@@ -71,7 +77,8 @@ template <typename T> struct EpiHessS {
   T nbar;
   const T* v;
   T* out;
-  __device__ void operator()(size_t i, T y, double*) const {
+  using Acc = AccD;
+  __device__ void operator()(size_t i, T y, Acc*) const {
     const T d = nbar * (w ? w[i] : (T)1) * exp(s[i]);
     out[i] = y + d * v[i];
   }
@@ -84,39 +91,50 @@ template <typename T> struct EpiHessD {
   const T* D;
   const T* v;
   T* out;
-  __device__ void operator()(size_t i, T y, double* acc) const {
+  using Acc = typename AccOf<T>::type;
+  __device__ void operator()(size_t i, T y, Acc* acc) const {
     const T vi = v[i];
     const T hv = y + D[i] * vi;
     out[i] = hv;
-    acc[0] += (double)vi * (double)hv;
+    acc[0].add(vi * hv);
   }
 };
 
 // Gradient g = S^-1 (s - mu) + nbar w e^s - N (Sec. 3.1.2) and the pieces of
-// -ln P: acc = { sum (s-mu) y, sum (D - N s), sum g^2, sum N s, sum N |s| }.
-template <typename T> struct EpiGrad {
-  static constexpr int NV = 5;
+// -ln P.  T: transform type; TS: type of s and w; TC: type of the CG fields.
+// Optionally writes g, the diagonal D = nbar w e^s and the CG start r = -g.
+// acc = { sum (s-mu) y, sum (D - N s), sum g^2, sum N s, sum N |s|,
+//         sum r M^-1 r }  with M = diag(D + c) (Jacobi) or I.
+template <typename T, typename TS, typename TC> struct EpiGrad {
+  static constexpr int NV = 6;
   static constexpr unsigned MAXMASK = 0;
-  const T* s;
-  const T* w;
+  using Acc = typename AccOf<T>::type;
+  const TS* s;
+  const TS* w;          // may be null
   const int32_t* N;
-  T nbar, mu;
-  T* g;                // may be null
-  T* D;                // may be null
-  float* D32;          // may be null: an FP32 copy of D for the mixed CG
-  __device__ void operator()(size_t i, T y, double* acc) const {
-    const T si = s[i];
-    const T d = nbar * (w ? w[i] : (T)1) * exp(si);
+  double nbar, mu;
+  T* g;                 // may be null
+  TC* D;                // may be null
+  TC* r;                // may be null
+  double c;             // Jacobi constant (S^-1)_ii
+  int jac;
+  __device__ void operator()(size_t i, T y, Acc* acc) const {
+    const TS si = s[i];
+    const T d = (T)nbar * (w ? (T)w[i] : (T)1) * exp((T)si);
     const T ni = (T)N[i];
     const T gi = y + d - ni;
     if (g) g[i] = gi;
-    if (D) D[i] = d;
-    if (D32) D32[i] = (float)d;
-    acc[0] += (double)(si - mu) * (double)y;
-    acc[1] += (double)d - (double)ni * (double)si;
-    acc[2] += (double)gi * (double)gi;
-    acc[3] += (double)ni * (double)si;
-    acc[4] += (double)ni * fabs((double)si);
+    if (D) D[i] = (TC)d;
+    if (r) r[i] = (TC)(-gi);
+    const T st = (T)si;
+    acc[0].add((st - (T)mu) * y);
+    acc[1].add(d - ni * st);
+    acc[2].add(gi * gi);
+    acc[3].add(ni * st);
+    acc[4].add(ni * (st < (T)0 ? -st : st));
+    // r^T M^-1 r in the precision of the CG fields
+    const TC gc = (TC)gi;
+    acc[5].add((T)(jac ? gc * gc / ((TC)d + (TC)c) : gc * gc));
   }
 };
 
@@ -125,8 +143,9 @@ template <typename T, typename TL> struct EpiDot {
   static constexpr int NV = 1;
   static constexpr unsigned MAXMASK = 0;
   const TL* lam;
-  __device__ void operator()(size_t i, T y, double* acc) const {
-    acc[0] += (double)lam[i] * (double)y;
+  using Acc = AccD;
+  __device__ void operator()(size_t i, T y, Acc* acc) const {
+    acc[0].add((double)lam[i] * (double)y);
   }
 };
 
@@ -142,7 +161,31 @@ template <int NV> struct FinStore {
   }
 };
 
-// alpha = r^T z / p^T H p; a non-positive curvature stops the CG.
+// After a gradient: store the sums and start CG on H xi = -g from xi = 0
+// (r = -g was written by the epilogue).  The CG tolerance and iteration cap
+// are arguments of the CG update.
+struct FinGrad {
+  __device__ void operator()(const double* t, DevScalars* sc) const {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sc->red[j] = t[j];
+    sc->rz = t[5];
+    sc->rr = t[2];
+    sc->bnorm2 = t[2];
+    sc->iter = 0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->breakdown = 0;
+    sc->xb = 0.0;
+    sc->xHx = 0.0;
+    sc->xmax = 0.0;
+    sc->done = t[2] <= 0.0 ? 1 : 0;
+  }
+};
+
+// alpha = r^T z / p^T H p; a non-positive curvature stops the CG.  Also
+// accumulates xi^T b = sum alpha_k r_k^T z_k and xi^T H xi =
+// sum alpha_k^2 p_k^T H p_k (H-conjugate directions): the two sums of the
+// step length of Eq. (New5).
 struct FinAlpha {
   __device__ void operator()(const double* t, DevScalars* sc) const {
     sc->pHp = t[0];
@@ -151,106 +194,90 @@ struct FinAlpha {
       sc->done = 1;
       sc->alpha = 0.0;
     } else {
-      sc->alpha = sc->rz / t[0];
+      const double a = sc->rz / t[0];
+      sc->alpha = a;
+      sc->xb += a * sc->rz;
+      sc->xHx += a * a * t[0];
     }
   }
 };
 
 // ------------------------------ CG kernels --------------------------------
-// Start CG on H x = b from x = 0: r = b (or -b), rz = r^T M^-1 r, rr = r^T r.
+// Start CG on H x = b from x = 0: r = b, rz = r^T M^-1 r, rr = r^T r.
 template <typename TC, typename TB, bool JAC>
 __global__ void __launch_bounds__(kThreads)
-k_cg_init(const TB* __restrict__ b, int negate, const TC* __restrict__ D, TC c,
-          TC* __restrict__ r, TC* __restrict__ x, size_t n3, RedArgs ra,
-          double rtol2, int max_iter) {
-  double acc[2] = {0.0, 0.0};
+k_cg_init(const TB* __restrict__ b, const TC* __restrict__ D, TC c, TC* __restrict__ r,
+          size_t n3, RedArgs ra) {
+  typename AccOf<TC>::type a0, a1;
+  a0.init(false);
+  a1.init(false);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
        i += (size_t)gridDim.x * blockDim.x) {
-    const TC ri = negate ? (TC)(-b[i]) : (TC)b[i];
+    const TC ri = (TC)b[i];
     r[i] = ri;
-    x[i] = (TC)0;
     const TC zi = JAC ? ri / (D[i] + c) : ri;
-    acc[0] += (double)ri * (double)zi;
-    acc[1] += (double)ri * (double)ri;
+    a0.add(ri * zi);
+    a1.add(ri * ri);
   }
+  double acc[2] = {a0.get(), a1.get()};
   struct Fin {
-    double rtol2; int max_iter;
     __device__ void operator()(const double* t, DevScalars* sc) const {
       sc->rz = t[0];
       sc->rr = t[1];
       sc->bnorm2 = t[1];
-      sc->rtol2 = rtol2;
       sc->iter = 0;
-      sc->max_iter = max_iter;
       sc->beta = 0.0;
       sc->alpha = 0.0;
       sc->breakdown = 0;
-      sc->done = (t[1] <= 0.0 || max_iter <= 0) ? 1 : 0;
-    }
-  };
-  block_reduce_finish<2, 0u>(acc, ra, Fin{rtol2, max_iter});
-}
-
-// x += alpha p, r -= alpha H p, then r^T M^-1 r and ||r||^2 for beta and the
-// stopping test ||r||^2 <= rtol^2 ||b||^2.
-template <typename TC, bool JAC>
-__global__ void __launch_bounds__(kThreads)
-k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
-            const TC* __restrict__ Hp, const TC* __restrict__ D, TC c, size_t n3,
-            RedArgs ra) {
-  if (ra.sc->done) return;
-  const TC alpha = (TC)ra.sc->alpha;
-  double acc[2] = {0.0, 0.0};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
-       i += (size_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const TC ri = r[i] - alpha * Hp[i];
-    r[i] = ri;
-    const TC zi = JAC ? ri / (D[i] + c) : ri;
-    acc[0] += (double)ri * (double)zi;
-    acc[1] += (double)ri * (double)ri;
-  }
-  struct Fin {
-    __device__ void operator()(const double* t, DevScalars* sc) const {
-      sc->beta = t[0] / sc->rz;
-      sc->rz = t[0];
-      sc->rr = t[1];
-      sc->iter += 1;
-      if (t[1] <= sc->rtol2 * sc->bnorm2 || sc->iter >= sc->max_iter) sc->done = 1;
+      sc->xb = 0.0;
+      sc->xHx = 0.0;
+      sc->xmax = 0.0;
+      sc->done = t[1] <= 0.0 ? 1 : 0;
     }
   };
   block_reduce_finish<2, 0u>(acc, ra, Fin{});
 }
 
-// Sums for the step length of Eq. (New5) and the line-search model:
-// { xi.g, xi.r, sum D xi^2, xi.D, xi.N, max |xi| }.
-template <typename TC, typename TG>
+// x += alpha p (x = alpha p on the first step, so x needs no clearing),
+// r -= alpha H p, then r^T M^-1 r, ||r||^2 and max |x| for beta, the
+// stopping test ||r||^2 <= rtol^2 ||b||^2 and the Newton step cap.
+template <typename TC, bool JAC>
 __global__ void __launch_bounds__(kThreads)
-k_dirstats(const TC* __restrict__ xi, const TG* __restrict__ g, const TC* __restrict__ r,
-           const TG* __restrict__ D, const int32_t* __restrict__ N, size_t n3, RedArgs ra) {
-  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, -INFINITY};
+k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
+            const TC* __restrict__ Hp, const TC* __restrict__ D, TC c, size_t n3,
+            RedArgs ra, double rtol2, int max_iter) {
+  if (ra.sc->done) return;
+  const TC alpha = (TC)ra.sc->alpha;
+  const bool first = ra.sc->iter == 0;
+  typename AccOf<TC>::type a0, a1, a2;
+  a0.init(false);
+  a1.init(false);
+  a2.init(true);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
        i += (size_t)gridDim.x * blockDim.x) {
-    const double x = (double)xi[i], d = (double)D[i];
-    acc[0] += x * (double)g[i];
-    acc[1] += x * (double)r[i];
-    acc[2] += d * x * x;
-    acc[3] += x * d;
-    acc[4] += x * (double)N[i];
-    acc[5] = fmax(acc[5], fabs(x));
+    const TC xn = first ? alpha * p[i] : x[i] + alpha * p[i];
+    x[i] = xn;
+    const TC ri = r[i] - alpha * Hp[i];
+    r[i] = ri;
+    const TC zi = JAC ? ri / (D[i] + c) : ri;
+    a0.add(ri * zi);
+    a1.add(ri * ri);
+    a2.max(xn < (TC)0 ? -xn : xn);
   }
-  block_reduce_finish<6, 1u << 5>(acc, ra, FinStore<6>{});
-}
-
-// Likelihood part of the line search: sum_i D_i exp(tau xi_i).
-template <typename TC, typename TG>
-__global__ void __launch_bounds__(kThreads)
-k_trial(const TC* __restrict__ xi, const TG* __restrict__ D, double tau, size_t n3, RedArgs ra) {
-  double acc[1] = {0.0};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
-       i += (size_t)gridDim.x * blockDim.x)
-    acc[0] += (double)D[i] * exp(tau * (double)xi[i]);
-  block_reduce_finish<1, 0u>(acc, ra, FinStore<1>{});
+  double acc[3] = {a0.get(), a1.get(), a2.get()};
+  struct Fin {
+    double rtol2;
+    int max_iter;
+    __device__ void operator()(const double* t, DevScalars* sc) const {
+      sc->beta = t[0] / sc->rz;
+      sc->rz = t[0];
+      sc->rr = t[1];
+      sc->xmax = t[2];
+      sc->iter += 1;
+      if (t[1] <= rtol2 * sc->bnorm2 || sc->iter >= max_iter) sc->done = 1;
+    }
+  };
+  block_reduce_finish<3, 1u << 2>(acc, ra, Fin{rtol2, max_iter});
 }
 
 // D = nbar w e^s (Sec. 3.1.2), from an FP64 s.

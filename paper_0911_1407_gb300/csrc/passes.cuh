@@ -240,9 +240,9 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
   }
   __syncthreads();
   fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
-  double acc[Epi::NV > 0 ? Epi::NV : 1];
+  typename Epi::Acc acc[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
-  for (int j = 0; j < Epi::NV; ++j) acc[j] = red_identity<Epi::MAXMASK>(j);
+  for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
   for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
     const int row = e / n, x = e - row * n;
     const C zz = a[x * G::P + (row >> 1)];
@@ -250,7 +250,12 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
     const size_t gi = ((size_t)z * n + (y0 + row)) * n + x;
     epi(gi, y, acc);
   }
-  if constexpr (Epi::NV > 0) block_reduce_finish<Epi::NV, Epi::MAXMASK>(acc, ra, fin);
+  if constexpr (Epi::NV > 0) {
+    double tot[Epi::NV];
+#pragma unroll
+    for (int j = 0; j < Epi::NV; ++j) tot[j] = acc[j].get();
+    block_reduce_finish<Epi::NV, Epi::MAXMASK>(tot, ra, fin);
+  }
 }
 
 }  // namespace plc

@@ -51,7 +51,9 @@ k_jacobi_constant(const double* __restrict__ M64, int n, RedArgs ra) {
 const char* const kSiteNames[S_NSITES] = {
     "xf_f64", "yf_f64", "z_f64", "yi_f64", "xi_f64",
     "xf_f32", "yf_f32", "z_f32", "yi_f32", "xi_f32",
-    "cg_init", "cg_update", "dirstats", "trial", "diag", "convert", "setup"};
+    "grad_xf_f64", "grad_yf_f64", "grad_z_f64", "grad_yi_f64", "grad_xi_f64",
+    "grad_xf_f32", "grad_yf_f32", "grad_z_f32", "grad_yi_f32", "grad_xi_f32",
+    "cg_init", "cg_update", "diag", "convert", "setup"};
 
 constexpr int kProfSlots = 512;
 
