@@ -13,7 +13,7 @@
 
 namespace plc {
 
-constexpr int kThreads = 256;          // threads per block of every kernel
+constexpr int kThreads = 256;          // threads per block (element-wise kernels and n <= 256)
 constexpr int kMaxStages = 12;
 constexpr int kMaxRed = 8;             // values per reduction
 
@@ -143,8 +143,10 @@ __device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
   }
 }
 
-// Full length-N transform of `nl` (<= L) lines.  On return `a` points at the
-// result and `b` at the free buffer.  Ends with a __syncthreads().
+// Full length-N transform of `nl` (<= L) lines, ping-ponging between two
+// buffers.  On return `a` points at the result and `b` at the free buffer.
+// Must be entered after a __syncthreads() that publishes the data; ends with
+// one.
 template <typename T, int SIGN, int L>
 __device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan,
                                           int nl, int P, const cpx<T>* tw) {
@@ -160,6 +162,23 @@ __device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan&
     cpx<T>* t = a; a = b; b = t;
     Ns *= R;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): every thread issues all of
+// its copies before waiting, so a tile's loads are all in flight at once
+// without passing through registers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async(float2* smem, const float2* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async(double2* smem, const double2* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------

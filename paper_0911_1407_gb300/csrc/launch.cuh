@@ -18,9 +18,9 @@ template <> inline const double* multiplier<double>(const plc_ctx* c) { return c
 
 // Raise a kernel's dynamic shared-memory limit to what the largest grid
 // (n = 512) needs, once per kernel instantiation.
-template <typename T, typename K> inline void set_smem(K kernel) {
+template <typename T, auto Kernel> inline void set_smem() {
   static const cudaError_t once = cudaFuncSetAttribute(
-      kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeom<T>::smem_bytes(512));
+      Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeom<T>::smem_bytes(512));
   check(once, "cudaFuncSetAttribute");
 }
 
@@ -31,19 +31,19 @@ template <typename T, typename Pro, typename Epi, typename Fin>
 void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done,
                   bool gradient_sites = false) {
   using G = PassGeom<T>;
+  const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
+                                : (sizeof(T) == 8 ? S_XF64 : S_XF32);
   const int n = c->n, h = n / 2 + 1;
   const size_t sm = G::smem_bytes(n);
   cpx<T>* A = static_cast<cpx<T>*>(c->specA);
   cpx<T>* B = static_cast<cpx<T>*>(c->specB);
   const cpx<T>* tw = twiddles<T>(c);
   const dim3 gx((n + G::RY - 1) / G::RY, n), gy((n + G::L - 1) / G::L, h);
-  const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
-                                : (sizeof(T) == 8 ? S_XF64 : S_XF32);
-  set_smem<T>(k_xf<T, Pro>);
-  set_smem<T>(k_yf<T>);
-  set_smem<T>(k_z<T>);
-  set_smem<T>(k_yi<T>);
-  set_smem<T>(k_xi<T, Epi, Fin>);
+  set_smem<T, k_xf<T, Pro>>();
+  set_smem<T, k_yf<T>>();
+  set_smem<T, k_z<T>>();
+  set_smem<T, k_yi<T>>();
+  set_smem<T, k_xi<T, Epi, Fin>>();
   {
     LaunchScope ls(c, Site(s0 + 0));
     k_xf<T, Pro><<<gx, kThreads, sm, c->stream>>>(pro, A, c->plan, tw, done);

@@ -199,8 +199,8 @@ extern "C" plc_status plc_hessvec_noalloc(int n, double box, const double* k, co
   k_yf<double><<<gy, kThreads, sm, st>>>(A, B, plan, tw, nullptr);
   k_z<double><<<gy, kThreads, sm, st>>>(B, M, 0, plan, tw, nullptr);
   k_yi<double><<<gy, kThreads, sm, st>>>(B, A, plan, tw, nullptr);
-  k_xi<double, Epi, FinNone><<<gx, kThreads, sm, st>>>(A, epi, FinNone{}, RedArgs{nullptr, nullptr},
-                                                       plan, tw, nullptr);
+  k_xi<double, Epi, FinNone><<<gx, kThreads, sm, st>>>(
+      A, epi, FinNone{}, RedArgs{nullptr, nullptr}, plan, tw, nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail(std::string("plc_hessvec_noalloc: launch: ") + cudaGetErrorString(e), PLC_ERR_CUDA);

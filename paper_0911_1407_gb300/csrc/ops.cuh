@@ -15,7 +15,7 @@ namespace plc {
 // ------------------------------- prologues --------------------------------
 template <typename T> struct ProLoad {
   const T* x;
-  __device__ T operator()(size_t i) const { return x[i]; }
+  __device__ T operator()(size_t i) const { return __ldg(x + i); }
 };
 
 // s - mu: the prior term of the gradient (Sec. 2.3, Eq. priorlog).  s may be
@@ -24,7 +24,7 @@ template <typename T, typename TS> struct ProShift {
   const TS* s;
   double mu;
   // difference taken in the transform precision (no FP64 work for float)
-  __device__ T operator()(size_t i) const { return (T)s[i] - (T)mu; }
+  __device__ T operator()(size_t i) const { return (T)__ldg(s + i) - (T)mu; }
 };
 
 // Newton update s <- s + dtau xi (Sec. 3.1), then s - mu for the gradient
@@ -36,7 +36,8 @@ template <typename T, typename TS, typename TX> struct ProStepShift {
   double dtau;
   double mu;
   __device__ T operator()(size_t i) const {
-    const TS sn = s[i] + (TS)dtau * (TS)xi[i];
+    // s[i] is read before this thread writes it and by no other thread
+    const TS sn = __ldg(s + i) + (TS)dtau * (TS)__ldg(xi + i);
     s[i] = sn;
     return (T)sn - (T)mu;
   }
@@ -51,9 +52,10 @@ template <typename T, bool JAC> struct ProCgDir {
   T* p;
   const DevScalars* sc;
   __device__ T operator()(size_t i) const {
-    const T beta = (T)sc->beta;
-    const T zi = JAC ? r[i] / (D[i] + c) : r[i];
-    const T pn = beta == (T)0 ? zi : zi + beta * p[i];
+    const T beta = (T)__ldg(&sc->beta);
+    const T ri = __ldg(r + i);
+    const T zi = JAC ? ri / (__ldg(D + i) + c) : ri;
+    const T pn = beta == (T)0 ? zi : zi + beta * __ldg(p + i);
     p[i] = pn;
     return pn;
   }
@@ -79,8 +81,8 @@ template <typename T> struct EpiHessS {
   T* out;
   using Acc = AccD;
   __device__ void operator()(size_t i, T y, Acc*) const {
-    const T d = nbar * (w ? w[i] : (T)1) * exp(s[i]);
-    out[i] = y + d * v[i];
+    const T d = nbar * (w ? __ldg(w + i) : (T)1) * exp(__ldg(s + i));
+    out[i] = y + d * __ldg(v + i);
   }
 };
 
@@ -93,8 +95,8 @@ template <typename T> struct EpiHessD {
   T* out;
   using Acc = typename AccOf<T>::type;
   __device__ void operator()(size_t i, T y, Acc* acc) const {
-    const T vi = v[i];
-    const T hv = y + D[i] * vi;
+    const T vi = __ldg(v + i);
+    const T hv = y + __ldg(D + i) * vi;
     out[i] = hv;
     acc[0].add(vi * hv);
   }
@@ -119,9 +121,9 @@ template <typename T, typename TS, typename TC> struct EpiGrad {
   double c;             // Jacobi constant (S^-1)_ii
   int jac;
   __device__ void operator()(size_t i, T y, Acc* acc) const {
-    const TS si = s[i];
-    const T d = (T)nbar * (w ? (T)w[i] : (T)1) * exp((T)si);
-    const T ni = (T)N[i];
+    const TS si = __ldg(s + i);
+    const T d = (T)nbar * (w ? (T)__ldg(w + i) : (T)1) * exp((T)si);
+    const T ni = (T)__ldg(N + i);
     const T gi = y + d - ni;
     if (g) g[i] = gi;
     if (D) D[i] = (TC)d;
@@ -145,7 +147,7 @@ template <typename T, typename TL> struct EpiDot {
   const TL* lam;
   using Acc = AccD;
   __device__ void operator()(size_t i, T y, Acc* acc) const {
-    acc[0].add((double)lam[i] * (double)y);
+    acc[0].add((double)__ldg(lam + i) * (double)y);
   }
 };
 

@@ -16,6 +16,13 @@
 // the transformed field on the fly (s - mu, a CG direction update, a Newton
 // step) and the epilogue fuses the pointwise tail (gradient of Sec. 3.1.2,
 // Hessian-vector product, dot products) into the last pass.
+//
+// Every block has all global loads of a tile in flight at once: the pure data
+// passes (YF, Z, YI) copy their tiles with cp.async straight into shared
+// memory, and XF / XI batch their loads in registers.  In A the spectra of
+// the two real rows packed into one complex line sit next to each other
+// (y = y0 + 2j, y0 + 2j + 1), so XF and XI move them as one vector and need
+// no staging tile.
 #pragma once
 
 #include "common.cuh"
@@ -26,12 +33,8 @@ template <typename T> struct PassGeom {
   static constexpr int L = Tile<T>::L;    // complex lines per tile
   static constexpr int P = L + 1;         // padded pitch of a tile row
   static constexpr int RY = 2 * L;        // real rows per x-pass tile
-  static constexpr int SP = RY + 1;       // pitch of the x-pass staging tile
-  // complex elements per ping-pong buffer
-  static __host__ __device__ int buf_elems(int n) {
-    int a = n * P, b = (n / 2 + 1) * SP;
-    return a > b ? a : b;
-  }
+  static __host__ __device__ int buf_elems(int n) { return n * P; }
+  // twiddles + two ping-pong line buffers
   static __host__ __device__ size_t smem_bytes(int n) {
     return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)buf_elems(n));
   }
@@ -42,6 +45,34 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* tw, const cpx<T>* __restri
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = twg[i];
 }
 
+// Two adjacent complex values as one (float) or two (double) 16-byte moves.
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) {
+  a = p[0];
+  b = p[1];
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
+
+#define PLC_PASS_PROLOGUE                                      \
+  using G = PassGeom<T>;                                       \
+  using C = cpx<T>;                                            \
+  if (done && *done) return;                                   \
+  extern __shared__ __align__(16) unsigned char smem_raw[];    \
+  C* tw = reinterpret_cast<C*>(smem_raw);                      \
+  C* a = tw + plan.n;                                          \
+  C* b = a + G::buf_elems(plan.n);                             \
+  load_twiddles<T>(tw, twg, plan.n)
+
 // ---------------------------------------------------------------------------
 // XF: r2c along x.  grid = (ceil(n / RY), n): block (yb, z) owns rows
 // y0 .. y0+RY-1 of plane z.  Rows 2j and 2j+1 form complex line j; after the
@@ -51,39 +82,41 @@ template <typename T, typename Pro>
 __global__ void __launch_bounds__(kThreads)
 k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ twg,
      const int* __restrict__ done) {
-  using G = PassGeom<T>;
-  using C = cpx<T>;
-  if (done && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PLC_PASS_PROLOGUE;
   const int n = plan.n, h = n / 2 + 1;
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* a = tw + n;
-  C* b = a + G::buf_elems(n);
   const int z = blockIdx.y, y0 = blockIdx.x * G::RY;
   const int rows = min(G::RY, n - y0);
   const int lines = rows >> 1;
-  load_twiddles<T>(tw, twg, n);
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-    const int row = e / n, x = e - row * n;
-    const size_t gi = ((size_t)z * n + (y0 + row)) * n + x;
-    T u = pro(gi);
-    reinterpret_cast<T*>(&a[x * G::P + (row >> 1)])[row & 1] = u;
+  const int total = rows * n;
+  constexpr int B8 = 8;
+  for (int base = threadIdx.x; base < total; base += B8 * kThreads) {
+    T u[B8];
+#pragma unroll
+    for (int k = 0; k < B8; ++k) {
+      const int e = base + k * kThreads;
+      if (e < total) {
+        const int row = e / n, x = e - row * n;
+        u[k] = pro(((size_t)z * n + (y0 + row)) * n + x);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B8; ++k) {
+      const int e = base + k * kThreads;
+      if (e < total) {
+        const int row = e / n, x = e - row * n;
+        reinterpret_cast<T*>(&a[x * G::P + (row >> 1)])[row & 1] = u[k];
+      }
+    }
   }
   __syncthreads();
   fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
-  C* st = b;
-  for (int e = threadIdx.x; e < h * lines; e += blockDim.x) {
+  for (int e = threadIdx.x; e < h * lines; e += kThreads) {
     const int k = e / lines, j = e - k * lines;
     const C zk = a[k * G::P + j];
     const C zc = cconj(a[((n - k) % n) * G::P + j]);
     const C s = cadd(zk, zc), d = csub(zk, zc);
-    st[k * G::SP + 2 * j] = cmk<C>((T)0.5 * s.x, (T)0.5 * s.y);
-    st[k * G::SP + 2 * j + 1] = cmk<C>((T)0.5 * d.y, (T)-0.5 * d.x);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < h * rows; e += blockDim.x) {
-    const int k = e / rows, row = e - k * rows;
-    A[((size_t)z * h + k) * n + y0 + row] = st[k * G::SP + row];
+    st_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], cmk<C>((T)0.5 * s.x, (T)0.5 * s.y),
+            cmk<C>((T)0.5 * d.y, (T)-0.5 * d.x));
   }
 }
 
@@ -95,24 +128,19 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, FftPlan plan,
      const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
-  using G = PassGeom<T>;
-  using C = cpx<T>;
-  if (done && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PLC_PASS_PROLOGUE;
   const int n = plan.n, h = n / 2 + 1;
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* a = tw + n;
-  C* b = a + G::buf_elems(n);
   const int z0 = blockIdx.x * G::L, kx = blockIdx.y;
   const int lines = min(G::L, n - z0);
-  load_twiddles<T>(tw, twg, n);
-  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+  const int total = lines * n;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = e / n, y = e - line * n;
-    a[y * G::P + line] = A[((size_t)(z0 + line) * h + kx) * n + y];
+    cp_async(&a[y * G::P + line], &A[((size_t)(z0 + line) * h + kx) * n + y]);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
-  for (int e = threadIdx.x; e < n * lines; e += blockDim.x) {
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = e / lines, line = e - ky * lines;
     B[((size_t)kx * n + ky) * n + z0 + line] = a[ky * G::P + line];
   }
@@ -128,38 +156,33 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_z(cpx<T>* __restrict__ B, const T* __restrict__ M, int zero_dc, FftPlan plan,
     const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
-  using G = PassGeom<T>;
-  using C = cpx<T>;
-  if (done && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PLC_PASS_PROLOGUE;
   const int n = plan.n;
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* a = tw + n;
-  C* b = a + G::buf_elems(n);
   const int ky0 = blockIdx.x * G::L, kx = blockIdx.y;
   const int lines = min(G::L, n - ky0);
-  load_twiddles<T>(tw, twg, n);
   const size_t base = ((size_t)kx * n + ky0) * n;
-  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+  const int total = lines * n;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = e / n, zz = e - line * n;
-    a[zz * G::P + line] = B[base + (size_t)line * n + zz];
+    cp_async(&a[zz * G::P + line], &B[base + e]);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
-  for (int e = threadIdx.x; e < n * lines; e += blockDim.x) {
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int kz = e / lines, line = e - kz * lines;
     const int ky = ky0 + line;
     const int my = min(ky, n - ky), mz = min(kz, n - kz);
     const int m2 = kx * kx + my * my + mz * mz;
-    T f = M[m2];
+    T f = __ldg(M + m2);
     if (zero_dc && m2 == 0) f = (T)0;
     a[kz * G::P + line] = cscale(a[kz * G::P + line], f);
   }
   __syncthreads();
   fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
-  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = e / n, zz = e - line * n;
-    B[base + (size_t)line * n + zz] = a[zz * G::P + line];
+    B[base + e] = a[zz * G::P + line];
   }
 }
 
@@ -170,24 +193,19 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, FftPlan plan,
      const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
-  using G = PassGeom<T>;
-  using C = cpx<T>;
-  if (done && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PLC_PASS_PROLOGUE;
   const int n = plan.n, h = n / 2 + 1;
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* a = tw + n;
-  C* b = a + G::buf_elems(n);
   const int z0 = blockIdx.x * G::L, kx = blockIdx.y;
   const int lines = min(G::L, n - z0);
-  load_twiddles<T>(tw, twg, n);
-  for (int e = threadIdx.x; e < n * lines; e += blockDim.x) {
+  const int total = lines * n;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = e / lines, line = e - ky * lines;
-    a[ky * G::P + line] = B[((size_t)kx * n + ky) * n + z0 + line];
+    cp_async(&a[ky * G::P + line], &B[((size_t)kx * n + ky) * n + z0 + line]);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
-  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = e / n, y = e - line * n;
     A[((size_t)(z0 + line) * h + kx) * n + y] = a[y * G::P + line];
   }
@@ -205,50 +223,47 @@ template <typename T, typename Epi, typename Fin>
 __global__ void __launch_bounds__(kThreads)
 k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
      const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
-  using G = PassGeom<T>;
-  using C = cpx<T>;
-  if (done && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = plan.n, h = n / 2 + 1;
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* a = tw + n;
-  C* b = a + G::buf_elems(n);
+  PLC_PASS_PROLOGUE;
+  const int n = plan.n, h = n / 2 + 1, nh = n / 2;
   const int z = blockIdx.y, y0 = blockIdx.x * G::RY;
   const int rows = min(G::RY, n - y0);
   const int lines = rows >> 1;
-  load_twiddles<T>(tw, twg, n);
-  C* st = b;
-  for (int e = threadIdx.x; e < h * rows; e += blockDim.x) {
-    const int k = e / rows, row = e - k * rows;
-    st[k * G::SP + row] = A[((size_t)z * h + k) * n + y0 + row];
-  }
-  __syncthreads();
-  const int nh = n / 2;
-  for (int e = threadIdx.x; e < n * lines; e += blockDim.x) {
-    const int k = e / lines, j = e - k * lines;
-    C v;
-    if (k <= nh) {
-      C xa = st[k * G::SP + 2 * j], xb = st[k * G::SP + 2 * j + 1];
-      if (k == 0 || k == nh) { xa.y = (T)0; xb.y = (T)0; }
-      v = cmk<C>(xa.x - xb.y, xa.y + xb.x);
-    } else {
-      const int kk = n - k;
-      const C xa = st[kk * G::SP + 2 * j], xb = st[kk * G::SP + 2 * j + 1];
-      v = cmk<C>(xa.x + xb.y, xb.x - xa.y);
+  const int npairs = h * lines;
+  constexpr int B4 = 4;
+  for (int base = threadIdx.x; base < npairs; base += B4 * kThreads) {
+    C xa[B4], xb[B4];
+#pragma unroll
+    for (int q = 0; q < B4; ++q) {
+      const int e = base + q * kThreads;
+      if (e < npairs) {
+        const int k = e / lines, j = e - k * lines;
+        ld_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], xa[q], xb[q]);
+      }
     }
-    a[k * G::P + j] = v;
+#pragma unroll
+    for (int q = 0; q < B4; ++q) {
+      const int e = base + q * kThreads;
+      if (e < npairs) {
+        const int k = e / lines, j = e - k * lines;
+        C va = xa[q], vb = xb[q];
+        if (k == 0 || k == nh) { va.y = (T)0; vb.y = (T)0; }
+        a[k * G::P + j] = cmk<C>(va.x - vb.y, va.y + vb.x);
+        if (k > 0 && k < nh) a[(n - k) * G::P + j] = cmk<C>(va.x + vb.y, vb.x - va.y);
+      }
+    }
   }
   __syncthreads();
   fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
   typename Epi::Acc acc[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
   for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+  const int total = rows * n;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < total; e += kThreads) {
     const int row = e / n, x = e - row * n;
     const C zz = a[x * G::P + (row >> 1)];
     const T y = (row & 1) ? zz.y : zz.x;
-    const size_t gi = ((size_t)z * n + (y0 + row)) * n + x;
-    epi(gi, y, acc);
+    epi(((size_t)z * n + (y0 + row)) * n + x, y, acc);
   }
   if constexpr (Epi::NV > 0) {
     double tot[Epi::NV];
@@ -257,5 +272,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
     block_reduce_finish<Epi::NV, Epi::MAXMASK>(tot, ra, fin);
   }
 }
+
+#undef PLC_PASS_PROLOGUE
 
 }  // namespace plc
