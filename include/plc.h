@@ -117,7 +117,9 @@ typedef struct {
   int cg_iters;        /* total CG iterations */
   int hv_count;        /* Hessian-vector products applied */
   int grad_evals;      /* gradient evaluations, line-search trials included */
-  int grad_evals_fp64; /* of which evaluated with FP64 transforms */
+  int grad_ffts;       /* of which evaluated through the FFT (the others carry
+                          S^-1 (s - mu) forward from the CG) */
+  int grad_ffts_fp64;  /* of those, with FP64 transforms */
   double grad_rel;     /* final ||g|| / ||g0|| */
   double g0_norm;      /* ||g0|| used */
   double neg_logpost;  /* final -ln P(s|N) (constants dropped) */
@@ -129,7 +131,9 @@ plc_status plc_default_opts(plc_opts* opts);
 
 /* MAP by inexact Newton-Krylov (Sec. 3.1): s <- s + tau xi with tau from
  * Eq. (New5), xi from preconditioned CG on H xi = -g, a step cap and an
- * Armijo backtracking line search whose trials are gradient evaluations.  s_inout (double, device) holds the start
+ * Armijo backtracking line search.  The prior term S^-1 (s - mu) is taken
+ * through the FFT at the start (and, for PLC_MIXED, once when the state moves
+ * from FP32 to FP64) and otherwise carried forward with S^-1 xi from the CG.  s_inout (double, device) holds the start
  * point on entry (e.g. filled with mu) and the MAP on exit.  N: int32 field;
  * w: double field or NULL (double in both precisions).  opts NULL = defaults;
  * stats may be NULL.  Returns PLC_ERR_NOT_CONVERGED with s_inout holding the

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("hv_count", ctypes.c_int), ("grad_evals", ctypes.c_int),
-                ("grad_evals_fp64", ctypes.c_int), ("grad_rel", ctypes.c_double), ("g0_norm", ctypes.c_double),
+                ("grad_ffts", ctypes.c_int), ("grad_ffts_fp64", ctypes.c_int),
+                ("grad_rel", ctypes.c_double), ("g0_norm", ctypes.c_double),
                 ("neg_logpost", ctypes.c_double), ("ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:

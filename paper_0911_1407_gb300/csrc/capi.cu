@@ -51,7 +51,15 @@ plc::FftPlan make_plan(int n) {
   if (rem == 4) { r.push_back(4); r.push_back(4); }
   for (int i = 0; i < b; ++i) r.push_back(3);
   p.nst = (int)r.size();
-  for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
+  int ns = 1;
+  for (int i = 0; i < p.nst; ++i) {
+    p.rad[i] = r[i];
+    p.ns[i] = ns;
+    p.tstep[i] = n / (ns * r[i]);
+    p.ns_m[i] = ns > 1 ? plc::make_fastdiv(ns).m : 0u;
+    ns *= r[i];
+  }
+  p.nd = plc::make_fastdiv(n);
   return p;
 }
 
@@ -67,22 +75,18 @@ template <typename T> void dalloc(T** p, size_t bytes) {
 void release(plc_ctx* c) {
   plc::profile_release(c);
   void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->M64, c->M32, c->lk, c->lP,
-                  c->sc, c->partials, c->f_g, c->f_D, c->f_D32, c->f_r, c->f_x, c->f_p, c->f_Hp};
+                  c->sc, c->partials};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : c->wf)
     if (p) cudaFree(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
 }
 
 void ensure_work_fields(plc_ctx* c) {
-  if (c->f_g) return;
   const size_t b = sizeof(double) * c->n3();
-  dalloc(&c->f_g, b);
-  dalloc(&c->f_D, b);
-  dalloc(&c->f_D32, sizeof(float) * c->n3());
-  dalloc(&c->f_r, b);
-  dalloc(&c->f_x, b);
-  dalloc(&c->f_p, b);
-  dalloc(&c->f_Hp, b);
+  for (void*& p : c->wf)
+    if (!p) dalloc(&p, b);
 }
 
 // Run `body`; map CUDA errors and allocation failures to status codes.

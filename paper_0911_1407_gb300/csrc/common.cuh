@@ -25,10 +25,25 @@ template <typename T> using cpx = typename CplxOf<T>::type;
 // Lines per shared-memory tile: 128 bytes of complex values per tile row.
 template <typename T> struct Tile { static constexpr int L = 128 / (2 * (int)sizeof(T)); };
 
+// Division by a runtime divisor d >= 2 as one multiply-high:
+// q = umulhi(x, m) with m = ceil(2^32 / d) equals floor(x / d) whenever
+// x * d < 2^32 (here x < 2^16 and d <= 512).
+struct FastDiv {
+  unsigned d, m;
+};
+inline __host__ __device__ FastDiv make_fastdiv(unsigned d) {
+  return FastDiv{d, (unsigned)((0x100000000ull + d - 1) / d)};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) { return __umulhi(x, f.m); }
+
 struct FftPlan {
   int n;                     // transform length (the grid side)
   int nst;                   // number of radix stages
   int rad[kMaxStages];       // radix of each stage (2, 3, 4 or 8)
+  int ns[kMaxStages];        // product of the radices before each stage
+  int tstep[kMaxStages];     // twiddle index step n / (ns * rad)
+  unsigned ns_m[kMaxStages]; // fast-division multiplier for ns (0 when ns = 1)
+  FastDiv nd;                // division by n
 };
 
 // Device-resident scalars of the solver (one instance per context).
@@ -111,17 +126,16 @@ template <typename T, int SIGN> struct Dft {
 template <typename T, int R, int SIGN, int L>
 __device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
                                                cpx<T>* __restrict__ out, int N,
-                                               int Ns, int nl, int P,
+                                               int Ns, unsigned ns_m, int tstep, int nl, int P,
                                                const cpx<T>* __restrict__ tw) {
   using C = cpx<T>;
   const int NR = N / R;
-  const int tstep = N / (Ns * R);
   const int total = L * NR;
   for (int b = threadIdx.x; b < total; b += blockDim.x) {
     const int c = b % L;
     const int j = b / L;
     if (c >= nl) continue;
-    const int k = j % Ns;
+    const int k = ns_m ? j - (int)__umulhi((unsigned)j, ns_m) * Ns : 0;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[(j + r * NR) * P + c];
@@ -150,17 +164,16 @@ __device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
 template <typename T, int SIGN, int L>
 __device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan,
                                           int nl, int P, const cpx<T>* tw) {
-  int Ns = 1;
   const int N = plan.n;
   for (int s = 0; s < plan.nst; ++s) {
-    const int R = plan.rad[s];
-    if (R == 8) stockham_stage<T, 8, SIGN, L>(a, b, N, Ns, nl, P, tw);
-    else if (R == 4) stockham_stage<T, 4, SIGN, L>(a, b, N, Ns, nl, P, tw);
-    else if (R == 2) stockham_stage<T, 2, SIGN, L>(a, b, N, Ns, nl, P, tw);
-    else stockham_stage<T, 3, SIGN, L>(a, b, N, Ns, nl, P, tw);
+    const int R = plan.rad[s], Ns = plan.ns[s], ts = plan.tstep[s];
+    const unsigned m = plan.ns_m[s];
+    if (R == 8) stockham_stage<T, 8, SIGN, L>(a, b, N, Ns, m, ts, nl, P, tw);
+    else if (R == 4) stockham_stage<T, 4, SIGN, L>(a, b, N, Ns, m, ts, nl, P, tw);
+    else if (R == 2) stockham_stage<T, 2, SIGN, L>(a, b, N, Ns, m, ts, nl, P, tw);
+    else stockham_stage<T, 3, SIGN, L>(a, b, N, Ns, m, ts, nl, P, tw);
     __syncthreads();
     cpx<T>* t = a; a = b; b = t;
-    Ns *= R;
   }
 }
 

@@ -21,7 +21,7 @@ enum Site {
   // pipelines of the Newton gradient (and line-search trials)
   S_GXF64, S_GYF64, S_GZ64, S_GYI64, S_GXI64,
   S_GXF32, S_GYF32, S_GZ32, S_GYI32, S_GXI32,
-  S_CG_INIT, S_CG_UPDATE, S_DIAG, S_CONVERT, S_SETUP,
+  S_CG_INIT, S_CG_UPDATE, S_NEWTON_UPDATE, S_DIAG, S_CONVERT, S_SETUP,
   S_NSITES
 };
 extern const char* const kSiteNames[S_NSITES];
@@ -70,14 +70,9 @@ struct plc_ctx {
   double* partials = nullptr;
   size_t partial_blocks = 0;
 
-  // Solver work fields (sized for double), allocated on first use.
-  void* f_g = nullptr;
-  void* f_D = nullptr;
-  void* f_D32 = nullptr;
-  void* f_r = nullptr;
-  void* f_x = nullptr;
-  void* f_p = nullptr;
-  void* f_Hp = nullptr;
+  // Solver work fields, each n^3 doubles, allocated on first use.
+  static constexpr int kNumWork = 13;
+  void* wf[kNumWork] = {};
 
   plc::Profiler prof;
   std::string err;
@@ -102,12 +97,16 @@ template <typename T> void hessvec_s(plc_ctx* c, const T* s, const T* w, double 
 // Public gradient: g (may be null) and the sums of -ln P (FP64).
 template <typename T> void grad_public(plc_ctx* c, const T* s, const T* w, const int32_t* N,
                                        double nbar, T* g);
-// Newton gradient at s (after s += dtau xi when xi is not null), in transform
-// type T; writes D and r = -g in the CG type TC and starts the CG solve.
-template <typename T, typename TC> void grad_newton(plc_ctx* c, double* s, const TC* xi,
-                                                    double dtau, const double* w,
-                                                    const int32_t* N, double nbar, TC* D, TC* r,
-                                                    bool jac);
+// Newton gradient at s through the FFT, in transform type T (s held as TS);
+// writes y = S^-1 (s - mu), g, D and r = -g (CG type TC) and starts the CG.
+template <typename T, typename TS, typename TC>
+void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar, T* y,
+                 T* g, TC* D, TC* r, bool jac);
+// Newton trial point s + tau xi without an FFT (see k_newton_update).
+template <typename T, typename TC>
+void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
+                   const TC* D, const int32_t* N, const double* w, double nbar, double tau,
+                   bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2);
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac);
 template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL* lam);
 

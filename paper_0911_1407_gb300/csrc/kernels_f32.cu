@@ -1,6 +1,6 @@
 // kernels_f32.cu -- FP32 instantiations: the PLC_MIXED operators, the FP32
-// gradients of the mixed solve's first phase and its FP32 conjugate-gradient
-// inner solve (FP64 reductions throughout).
+// phase of the mixed solve and its FP32 conjugate-gradient inner solve
+// (FP64 reductions throughout).
 #include "launch.cuh"
 
 namespace plc {
@@ -8,8 +8,13 @@ template void prior_apply<float>(plc_ctx*, const float*, float*);
 template void hessvec_s<float>(plc_ctx*, const float*, const float*, double, const float*, float*);
 template void grad_public<float>(plc_ctx*, const float*, const float*, const int32_t*, double,
                                  float*);
-template void grad_newton<float, float>(plc_ctx*, double*, const float*, double, const double*,
-                                        const int32_t*, double, float*, float*, bool);
+template void grad_newton<float, float, float>(plc_ctx*, const float*, const double*,
+                                               const int32_t*, double, float*, float*, float*,
+                                               float*, bool);
+template void newton_update<float, float>(plc_ctx*, const float*, const float*, const float*,
+                                          const float*, const float*, const float*,
+                                          const int32_t*, const double*, double, double, bool,
+                                          float*, float*, float*, float*, float*);
 template void cg_hv<float>(plc_ctx*, const float*, const float*, float*, float*, bool);
 template void vjp_amplitude<float>(plc_ctx*, const double*, const float*);
 template void cg_init<float>(plc_ctx*, const double*, const float*, float*, bool);
@@ -17,4 +22,5 @@ template void cg_update<float>(plc_ctx*, float*, float*, const float*, const flo
                                bool, double, int);
 template void diag<float>(plc_ctx*, const double*, const double*, double, float*);
 template void convert<double, float>(plc_ctx*, const float*, double*);
+template void convert<float, double>(plc_ctx*, const double*, float*);
 }  // namespace plc

@@ -79,20 +79,18 @@ template <typename T> void hessvec_s(plc_ctx* c, const T* s, const T* w, double 
 template <typename T> void grad_public(plc_ctx* c, const T* s, const T* w, const int32_t* N,
                                        double nbar, T* g) {
   run_pipeline<T>(c, ProShift<T, T>{s, c->mu},
-                  EpiGrad<T, T, T>{s, w, N, nbar, c->mu, g, nullptr, nullptr, c->jac_c, 0},
+                  EpiGrad<T, T, T, T>{s, w, N, nbar, c->mu, nullptr, g, nullptr, nullptr,
+                                      c->jac_c, 0},
                   FinStore<6>{}, 0, nullptr, true);
 }
 
-template <typename T, typename TC> void grad_newton(plc_ctx* c, double* s, const TC* xi,
-                                                    double dtau, const double* w,
-                                                    const int32_t* N, double nbar, TC* D, TC* r,
-                                                    bool jac) {
-  const EpiGrad<T, double, TC> epi{s, w, N, nbar, c->mu, nullptr, D, r, c->jac_c, jac ? 1 : 0};
-  if (xi)
-    run_pipeline<T>(c, ProStepShift<T, double, TC>{s, xi, dtau, c->mu}, epi, FinGrad{}, 0,
-                    nullptr, true);
-  else
-    run_pipeline<T>(c, ProShift<T, double>{s, c->mu}, epi, FinGrad{}, 0, nullptr, true);
+template <typename T, typename TS, typename TC>
+void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar, T* y,
+                 T* g, TC* D, TC* r, bool jac) {
+  run_pipeline<T>(c, ProShift<T, TS>{s, c->mu},
+                  EpiGrad<T, TS, double, TC>{s, w, N, nbar, c->mu, y, g, D, r, c->jac_c,
+                                             jac ? 1 : 0},
+                  FinGrad{}, 0, nullptr, true);
 }
 
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac) {
@@ -135,6 +133,17 @@ template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, con
     k_cg_update<TC, false><<<nb, kThreads, 0, c->stream>>>(x, r, p, Hp, D, (TC)c->jac_c, c->n3(),
                                                             red_args(c), rtol2, max_iter);
   check(cudaGetLastError(), "k_cg_update");
+}
+
+template <typename T, typename TC>
+void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
+                   const TC* D, const int32_t* N, const double* w, double nbar, double tau,
+                   bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2) {
+  LaunchScope ls(c, S_NEWTON_UPDATE);
+  k_newton_update<T, TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(
+      s, y, g, r, xi, D, N, w, nbar, c->mu, tau, c->jac_c, jac ? 1 : 0, s2, y2, g2, D2, r2,
+      c->n3(), red_args(c));
+  check(cudaGetLastError(), "k_newton_update");
 }
 
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D) {

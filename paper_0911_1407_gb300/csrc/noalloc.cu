@@ -107,6 +107,14 @@ plc::FftPlan noalloc_plan(int n) {
   if (rem == 4) { p.rad[k++] = 4; p.rad[k++] = 4; }
   for (int i = 0; i < b; ++i) p.rad[k++] = 3;
   p.nst = k;
+  int ns = 1;
+  for (int i = 0; i < k; ++i) {
+    p.ns[i] = ns;
+    p.tstep[i] = n / (ns * p.rad[i]);
+    p.ns_m[i] = ns > 1 ? plc::make_fastdiv(ns).m : 0u;
+    ns *= p.rad[i];
+  }
+  p.nd = plc::make_fastdiv(n);
   return p;
 }
 

@@ -27,22 +27,6 @@ template <typename T, typename TS> struct ProShift {
   __device__ T operator()(size_t i) const { return (T)__ldg(s + i) - (T)mu; }
 };
 
-// Newton update s <- s + dtau xi (Sec. 3.1), then s - mu for the gradient
-// at the new point.  Backtracking re-applies the difference of two step
-// lengths, so dtau may be negative.
-template <typename T, typename TS, typename TX> struct ProStepShift {
-  TS* s;
-  const TX* xi;
-  double dtau;
-  double mu;
-  __device__ T operator()(size_t i) const {
-    // s[i] is read before this thread writes it and by no other thread
-    const TS sn = __ldg(s + i) + (TS)dtau * (TS)__ldg(xi + i);
-    s[i] = sn;
-    return (T)sn - (T)mu;
-  }
-};
-
 // CG search direction p <- M^-1 r + beta p (beta from the device scalars;
 // beta = 0 on the first step, where p is not read).
 template <typename T, bool JAC> struct ProCgDir {
@@ -103,32 +87,34 @@ template <typename T> struct EpiHessD {
 };
 
 // Gradient g = S^-1 (s - mu) + nbar w e^s - N (Sec. 3.1.2) and the pieces of
-// -ln P.  T: transform type; TS: type of s and w; TC: type of the CG fields.
-// Optionally writes g, the diagonal D = nbar w e^s and the CG start r = -g.
+// -ln P.  T: transform type; TS: type of s; TW: type of w; TC: type of the CG
+// fields.  Optionally writes y = S^-1 (s - mu), g, the diagonal
+// D = nbar w e^s and the CG start r = -g.
 // acc = { sum (s-mu) y, sum (D - N s), sum g^2, sum N s, sum N |s|,
 //         sum r M^-1 r }  with M = diag(D + c) (Jacobi) or I.
-template <typename T, typename TS, typename TC> struct EpiGrad {
+template <typename T, typename TS, typename TW, typename TC> struct EpiGrad {
   static constexpr int NV = 6;
   static constexpr unsigned MAXMASK = 0;
   using Acc = typename AccOf<T>::type;
   const TS* s;
-  const TS* w;          // may be null
+  const TW* w;          // may be null
   const int32_t* N;
   double nbar, mu;
+  T* yout;              // may be null
   T* g;                 // may be null
   TC* D;                // may be null
   TC* r;                // may be null
   double c;             // Jacobi constant (S^-1)_ii
   int jac;
   __device__ void operator()(size_t i, T y, Acc* acc) const {
-    const TS si = __ldg(s + i);
-    const T d = (T)nbar * (w ? (T)__ldg(w + i) : (T)1) * exp((T)si);
+    const T st = (T)__ldg(s + i);
+    const T d = (T)nbar * (w ? (T)__ldg(w + i) : (T)1) * exp(st);
     const T ni = (T)__ldg(N + i);
     const T gi = y + d - ni;
+    if (yout) yout[i] = y;
     if (g) g[i] = gi;
     if (D) D[i] = (TC)d;
     if (r) r[i] = (TC)(-gi);
-    const T st = (T)si;
     acc[0].add((st - (T)mu) * y);
     acc[1].add(d - ni * st);
     acc[2].add(gi * gi);
@@ -280,6 +266,56 @@ k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
     }
   };
   block_reduce_finish<3, 1u << 2>(acc, ra, Fin{rtol2, max_iter});
+}
+
+// A Newton trial point without an FFT.  S^-1 is linear, so with the CG's
+// own quantities, S^-1 xi = H xi - D xi = (b - r) - D xi (b = -g the CG
+// right-hand side, r its recursively updated residual), and at
+// s' = s + tau xi:
+//   y' = y + tau S^-1 xi,   D' = nbar w e^{s'},   g' = y' + D' - N.
+// The increment carries the rounding of the CG fields relative to the
+// current gradient only.  Writes the trial state to separate buffers (the
+// line search may reject it) and the sums of EpiGrad, finalised by FinGrad.
+template <typename T, typename TC>
+__global__ void __launch_bounds__(kThreads)
+k_newton_update(const T* __restrict__ s, const T* __restrict__ y, const T* __restrict__ g,
+                const TC* __restrict__ r, const TC* __restrict__ xi, const TC* __restrict__ D,
+                const int32_t* __restrict__ N, const double* __restrict__ w, double nbar,
+                double mu, double tau, double c, int jac, T* __restrict__ s2,
+                T* __restrict__ y2, T* __restrict__ g2, TC* __restrict__ D2,
+                TC* __restrict__ r2, size_t n3, RedArgs ra) {
+  using Acc = typename AccOf<T>::type;
+  Acc acc[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) acc[j].init(false);
+  const T tt = (T)tau;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const TC xi_i = xi[i];
+    const TC b_i = (TC)(-g[i]);
+    const TC sinv_xi = b_i - r[i] - D[i] * xi_i;
+    const T yn = y[i] + tt * (T)sinv_xi;
+    const T sn = s[i] + tt * (T)xi_i;
+    const T d = (T)nbar * (w ? (T)w[i] : (T)1) * exp(sn);
+    const T ni = (T)N[i];
+    const T gn = yn + d - ni;
+    s2[i] = sn;
+    y2[i] = yn;
+    g2[i] = gn;
+    D2[i] = (TC)d;
+    r2[i] = (TC)(-gn);
+    acc[0].add((sn - (T)mu) * yn);
+    acc[1].add(d - ni * sn);
+    acc[2].add(gn * gn);
+    acc[3].add(ni * sn);
+    acc[4].add(ni * (sn < (T)0 ? -sn : sn));
+    const TC gc = (TC)gn;
+    acc[5].add((T)(jac ? gc * gc / ((TC)d + (TC)c) : gc * gc));
+  }
+  double tot[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) tot[j] = acc[j].get();
+  block_reduce_finish<6, 0u>(tot, ra, FinGrad{});
 }
 
 // D = nbar w e^s (Sec. 3.1.2), from an FP64 s.

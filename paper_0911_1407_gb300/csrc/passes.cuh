@@ -95,7 +95,7 @@ k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ t
     for (int k = 0; k < B8; ++k) {
       const int e = base + k * kThreads;
       if (e < total) {
-        const int row = e / n, x = e - row * n;
+        const int row = fdiv(e, plan.nd), x = e - row * n;
         u[k] = pro(((size_t)z * n + (y0 + row)) * n + x);
       }
     }
@@ -103,17 +103,18 @@ k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ t
     for (int k = 0; k < B8; ++k) {
       const int e = base + k * kThreads;
       if (e < total) {
-        const int row = e / n, x = e - row * n;
+        const int row = fdiv(e, plan.nd), x = e - row * n;
         reinterpret_cast<T*>(&a[x * G::P + (row >> 1)])[row & 1] = u[k];
       }
     }
   }
   __syncthreads();
   fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
+  const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < h * lines; e += kThreads) {
-    const int k = e / lines, j = e - k * lines;
+    const int k = fdiv(e, ld), j = e - k * lines;
     const C zk = a[k * G::P + j];
-    const C zc = cconj(a[((n - k) % n) * G::P + j]);
+    const C zc = cconj(a[(k ? n - k : 0) * G::P + j]);
     const C s = cadd(zk, zc), d = csub(zk, zc);
     st_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], cmk<C>((T)0.5 * s.x, (T)0.5 * s.y),
             cmk<C>((T)0.5 * d.y, (T)-0.5 * d.x));
@@ -134,14 +135,15 @@ k_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, FftPlan plan,
   const int lines = min(G::L, n - z0);
   const int total = lines * n;
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int line = e / n, y = e - line * n;
+    const int line = fdiv(e, plan.nd), y = e - line * n;
     cp_async(&a[y * G::P + line], &A[((size_t)(z0 + line) * h + kx) * n + y]);
   }
   cp_async_wait_all();
   __syncthreads();
   fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
+  const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int ky = e / lines, line = e - ky * lines;
+    const int ky = fdiv(e, ld), line = e - ky * lines;
     B[((size_t)kx * n + ky) * n + z0 + line] = a[ky * G::P + line];
   }
 }
@@ -163,14 +165,15 @@ k_z(cpx<T>* __restrict__ B, const T* __restrict__ M, int zero_dc, FftPlan plan,
   const size_t base = ((size_t)kx * n + ky0) * n;
   const int total = lines * n;
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int line = e / n, zz = e - line * n;
+    const int line = fdiv(e, plan.nd), zz = e - line * n;
     cp_async(&a[zz * G::P + line], &B[base + e]);
   }
   cp_async_wait_all();
   __syncthreads();
   fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
+  const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int kz = e / lines, line = e - kz * lines;
+    const int kz = fdiv(e, ld), line = e - kz * lines;
     const int ky = ky0 + line;
     const int my = min(ky, n - ky), mz = min(kz, n - kz);
     const int m2 = kx * kx + my * my + mz * mz;
@@ -181,7 +184,7 @@ k_z(cpx<T>* __restrict__ B, const T* __restrict__ M, int zero_dc, FftPlan plan,
   __syncthreads();
   fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int line = e / n, zz = e - line * n;
+    const int line = fdiv(e, plan.nd), zz = e - line * n;
     B[base + e] = a[zz * G::P + line];
   }
 }
@@ -198,15 +201,16 @@ k_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, FftPlan plan,
   const int z0 = blockIdx.x * G::L, kx = blockIdx.y;
   const int lines = min(G::L, n - z0);
   const int total = lines * n;
+  const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int ky = e / lines, line = e - ky * lines;
+    const int ky = fdiv(e, ld), line = e - ky * lines;
     cp_async(&a[ky * G::P + line], &B[((size_t)kx * n + ky) * n + z0 + line]);
   }
   cp_async_wait_all();
   __syncthreads();
   fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int line = e / n, y = e - line * n;
+    const int line = fdiv(e, plan.nd), y = e - line * n;
     A[((size_t)(z0 + line) * h + kx) * n + y] = a[y * G::P + line];
   }
 }
@@ -229,6 +233,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
   const int rows = min(G::RY, n - y0);
   const int lines = rows >> 1;
   const int npairs = h * lines;
+  const FastDiv ld = make_fastdiv(lines);
   constexpr int B4 = 4;
   for (int base = threadIdx.x; base < npairs; base += B4 * kThreads) {
     C xa[B4], xb[B4];
@@ -236,7 +241,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
     for (int q = 0; q < B4; ++q) {
       const int e = base + q * kThreads;
       if (e < npairs) {
-        const int k = e / lines, j = e - k * lines;
+        const int k = fdiv(e, ld), j = e - k * lines;
         ld_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], xa[q], xb[q]);
       }
     }
@@ -244,7 +249,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
     for (int q = 0; q < B4; ++q) {
       const int e = base + q * kThreads;
       if (e < npairs) {
-        const int k = e / lines, j = e - k * lines;
+        const int k = fdiv(e, ld), j = e - k * lines;
         C va = xa[q], vb = xb[q];
         if (k == 0 || k == nh) { va.y = (T)0; vb.y = (T)0; }
         a[k * G::P + j] = cmk<C>(va.x - vb.y, va.y + vb.x);
@@ -260,7 +265,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
   const int total = rows * n;
 #pragma unroll 4
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int row = e / n, x = e - row * n;
+    const int row = fdiv(e, plan.nd), x = e - row * n;
     const C zz = a[x * G::P + (row >> 1)];
     const T y = (row & 1) ? zz.y : zz.x;
     epi(((size_t)z * n + (y0 + row)) * n + x, y, acc);

@@ -3,23 +3,30 @@
 // them after each gradient and after each chunk of CG iterations.
 //
 // One Newton step:
-//   1. CG on H xi = -g (r = -g and r^T M^-1 r come from the gradient pass),
-//      to a relative residual eta = min(eta_max, sqrt(||g|| / ||g0||));
+//   1. CG on H xi = -g (r = -g and r^T M^-1 r come from the gradient), to a
+//      relative residual eta = min(eta_max, sqrt(||g|| / ||g0||));
 //   2. tau from Eq. (New5), tau = -xi^T g / xi^T H xi, with both sums taken
 //      from the CG recurrences (xi^T b = sum alpha_k r_k^T z_k,
 //      xi^T H xi = sum alpha_k^2 p_k^T H p_k), capped so max |tau xi| <=
 //      step_cap;
-//   3. Armijo backtracking in which every trial is a gradient evaluation at
-//      s + tau xi (its epilogue also returns -ln P), so the accepted trial
-//      leaves the next gradient, diagonal and CG start in place.
-// PLC_MIXED evaluates the gradient in FP32 while ||g|| / ||g0|| >=
-// mixed_switch and in FP64 after that; the stopping test is only passed on
-// an FP64 gradient.  The CG always runs in the precision of its fields (FP32
+//   3. Armijo backtracking.  A trial point s + tau xi needs no FFT: S^-1 is
+//      linear and the CG already holds S^-1 xi = (b - r) - D xi, so the
+//      prior term is carried forward, y' = y + tau S^-1 xi, and the trial
+//      gradient g' = y' + nbar w e^{s'} - N and -ln P come from one
+//      element-wise pass (k_newton_update).
+// y = S^-1 (s - mu) is evaluated through the FFT only at the start and, for
+// PLC_MIXED, once more when the solve moves from FP32 to FP64 state.  The
+// rounding of each carried increment is relative to the gradient at that
+// step, so after that FP64 refresh the gradient stays accurate to FP64
+// relative to ||g0|| (iterative refinement).  PLC_MIXED keeps s, y, g in FP32
+// while ||g|| / ||g0|| >= mixed_switch, in FP64 after that; the stopping test
+// is only passed in FP64.  The CG runs in the precision of its fields (FP32
 // for PLC_MIXED).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <type_traits>
+#include <utility>
 
 #include "ctx.h"
 #include "solver.h"
@@ -45,79 +52,123 @@ GradSums grad_sums(const plc_ctx* c) {
 }
 
 // Enqueue CG iterations in chunks until the device flags convergence,
-// breakdown or the iteration cap.  Returns the iterations performed.
+// breakdown or the iteration cap; chunks start at `first` iterations and
+// double (up to `chunk`), so few iterations are enqueued past the end.
+// Returns the iterations performed.
 template <typename TC>
 int run_cg(plc_ctx* c, TC* x, TC* r, TC* p, TC* Hp, const TC* D, bool jac, double rtol2,
-           int max_cg, int chunk) {
+           int max_cg, int chunk, int first) {
   int launched = 0;
+  int k = std::max(1, std::min(first, chunk));
   read_scalars(c);
   while (!c->sc_host->done && launched < max_cg) {
-    const int k = std::min(std::max(chunk, 1), max_cg - launched);
+    k = std::min(k, max_cg - launched);
     for (int i = 0; i < k; ++i) {
       cg_hv<TC>(c, r, D, p, Hp, jac);
       cg_update<TC>(c, x, r, p, Hp, D, jac, rtol2, max_cg);
     }
     launched += k;
     read_scalars(c);
+    k = std::min(2 * k, std::max(chunk, 1));
   }
   return c->sc_host->iter;
 }
 
-template <typename TC> TC* dfield(void* p) { return static_cast<TC*>(p); }
+template <typename T> T* as(void* p) { return static_cast<T*>(p); }
+
+// One set of Newton state fields: s, y = S^-1 (s - mu), g (precision of the
+// phase), the CG diagonal D and the CG start r = -g (CG precision).
+struct State {
+  void* s;
+  void* y;
+  void* g;
+  void* D;
+  void* r;
+};
 
 }  // namespace
 
 template <typename TC>
-plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar, double* s,
+plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar, double* s_out,
                       const plc_opts& o, plc_stats* st) {
   constexpr bool kMixed = std::is_same<TC, float>::value;
   const auto t0 = std::chrono::steady_clock::now();
-  TC* D = kMixed ? dfield<TC>(c->f_D32) : dfield<TC>(c->f_D);
-  TC* r = dfield<TC>(c->f_r);
-  TC* x = dfield<TC>(c->f_x);
-  TC* p = dfield<TC>(c->f_p);
-  TC* Hp = dfield<TC>(c->f_Hp);
+  void** F = c->wf;
+  TC* x = as<TC>(F[10]);
+  TC* p = as<TC>(F[11]);
+  TC* Hp = as<TC>(F[12]);
   const bool jac = o.precond == 1;
+  bool fp64 = !kMixed || !(o.mixed_switch < 1.0);
+  State cur{fp64 ? (void*)s_out : F[0], F[2], F[4], F[6], F[8]};
+  State alt{F[1], F[3], F[5], F[7], F[9]};
 
   plc_stats S{};
-  // Gradient at s (+ dtau xi); fp64 selects the transform precision.
-  auto gradient = [&](bool fp64, const TC* xi, double dtau) {
-    if constexpr (kMixed) {
-      if (fp64) grad_newton<double, TC>(c, s, xi, dtau, w, N, nbar, D, r, jac);
-      else grad_newton<float, TC>(c, s, xi, dtau, w, N, nbar, D, r, jac);
-    } else {
-      (void)fp64;
-      grad_newton<double, TC>(c, s, xi, dtau, w, N, nbar, D, r, jac);
+  // y, g, D, r and the sums at cur.s through the FFT (phase precision)
+  auto fft_gradient = [&]() {
+    if (fp64) {
+      grad_newton<double, double, TC>(c, as<double>(cur.s), w, N, nbar, as<double>(cur.y),
+                                      as<double>(cur.g), as<TC>(cur.D), as<TC>(cur.r), jac);
+      S.grad_ffts_fp64 += 1;
+    } else if constexpr (kMixed) {
+      grad_newton<float, float, float>(c, as<float>(cur.s), w, N, nbar, as<float>(cur.y),
+                                       as<float>(cur.g), as<float>(cur.D), as<float>(cur.r), jac);
     }
     read_scalars(c);
     S.grad_evals += 1;
-    if (fp64 || !kMixed) S.grad_evals_fp64 += 1;
+    S.grad_ffts += 1;
     return grad_sums(c);
+  };
+  auto trial = [&](double tau) {
+    if (fp64) {
+      newton_update<double, TC>(c, as<double>(cur.s), as<double>(cur.y), as<double>(cur.g),
+                                as<TC>(cur.r), x, as<TC>(cur.D), N, w, nbar, tau, jac,
+                                as<double>(alt.s), as<double>(alt.y), as<double>(alt.g),
+                                as<TC>(alt.D), as<TC>(alt.r));
+    } else if constexpr (kMixed) {
+      newton_update<float, float>(c, as<float>(cur.s), as<float>(cur.y), as<float>(cur.g),
+                                  as<float>(cur.r), x, as<float>(cur.D), N, w, nbar, tau, jac,
+                                  as<float>(alt.s), as<float>(alt.y), as<float>(alt.g),
+                                  as<float>(alt.D), as<float>(alt.r));
+    }
+    read_scalars(c);
+    S.grad_evals += 1;
+    return grad_sums(c);
+  };
+  // move the FP32 state to FP64: s in the caller's buffer, fresh FP64 gradient
+  auto to_fp64 = [&]() {
+    if constexpr (kMixed) convert<double, float>(c, as<float>(cur.s), s_out);
+    fp64 = true;
+    cur.s = s_out;
+    alt.s = F[1];
+    return fft_gradient();
   };
 
   reset_ticket(c);
-  bool fp64 = !kMixed || !(o.mixed_switch < 1.0);
-  GradSums gs = gradient(fp64, nullptr, 0.0);
+  if (!fp64) {
+    if constexpr (kMixed) convert<float, double>(c, s_out, as<float>(cur.s));
+  }
+  GradSums gs = fft_gradient();
   const double g0 = o.g0_norm > 0.0 ? o.g0_norm : std::sqrt(gs.gg);
   S.g0_norm = g0;
   plc_status status = PLC_OK;
-  int it = 0;
+  int it = 0, prev_cg = 1;
   for (;;) {
     const double gnorm = std::sqrt(gs.gg);
     if (!std::isfinite(gnorm) || !std::isfinite(gs.f())) { status = PLC_ERR_NONFINITE; break; }
     const double rel = g0 > 0.0 ? gnorm / g0 : 0.0;
     S.grad_rel = rel;
     S.neg_logpost = gs.f();
-    if (rel < o.tol) {
-      if (fp64) break;
-      fp64 = true;                       // confirm on an FP64 gradient at the same point
-      gs = gradient(true, nullptr, 0.0);
+    if (!fp64 && (rel < o.mixed_switch || rel < o.tol)) {
+      gs = to_fp64();
       continue;
     }
+    if (rel < o.tol) break;
     if (it >= o.max_newton) { status = PLC_ERR_NOT_CONVERGED; break; }
     // 1. inexact Newton direction
     const double eta = std::min(o.eta_max, std::sqrt(rel));
-    const int iters = run_cg<TC>(c, x, r, p, Hp, D, jac, eta * eta, o.max_cg, o.cg_chunk);
+    const int iters = run_cg<TC>(c, x, as<TC>(cur.r), p, Hp, as<TC>(cur.D), jac, eta * eta,
+                                 o.max_cg, o.cg_chunk, prev_cg);
+    prev_cg = iters;
     S.cg_iters += iters;
     S.hv_count += iters;
     if (iters == 0) {
@@ -128,20 +179,25 @@ plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar
     const double xg = -c->sc_host->xb, xHx = c->sc_host->xHx, xmax = c->sc_host->xmax;
     double tau = -xg / xHx;
     if (tau * xmax > o.step_cap) tau = o.step_cap / xmax;
-    // 3. Armijo backtracking on gradient evaluations at s + tau xi
-    const bool next_fp64 = fp64 || rel < o.mixed_switch;
-    const double eps = (fp64 && next_fp64) ? 1e-13 : 1e-6;   // rounding level of f
+    // 3. Armijo backtracking on element-wise trial points
+    const double eps = fp64 ? 1e-13 : 1e-6;     // rounding level of f
     const double f0 = gs.f(), scale = gs.scale();
-    double applied = 0.0;
     for (int q = 0; q < 30; ++q) {
-      gs = gradient(next_fp64, x, tau - applied);
-      applied = tau;
+      gs = trial(tau);
       if (gs.f() <= f0 + 1e-4 * tau * xg || -tau * xg < eps * scale) break;
       tau *= 0.5;
     }
-    fp64 = next_fp64;
+    std::swap(cur, alt);
     ++it;
   }
+  // leave the iterate in the caller's buffer
+  if (!fp64) {
+    if constexpr (kMixed) convert<double, float>(c, as<float>(cur.s), s_out);
+  } else if (cur.s != s_out) {
+    check(cudaMemcpyAsync(s_out, cur.s, sizeof(double) * c->n3(), cudaMemcpyDeviceToDevice,
+                          c->stream), "copy s");
+  }
+  check(cudaStreamSynchronize(c->stream), "stream synchronize");
   S.newton_iters = it;
   S.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = S;
@@ -153,18 +209,19 @@ plc_status map_vjp(plc_ctx* c, const double* s_map, const double* w, double nbar
                    double* vjp_N, double* vjp_lnA, const plc_opts& o, plc_stats* st) {
   constexpr bool kMixed = std::is_same<TC, float>::value;
   const auto t0 = std::chrono::steady_clock::now();
-  TC* D = kMixed ? dfield<TC>(c->f_D32) : dfield<TC>(c->f_D);
-  TC* r = dfield<TC>(c->f_r);
-  TC* x = dfield<TC>(c->f_x);
-  TC* p = dfield<TC>(c->f_p);
-  TC* Hp = dfield<TC>(c->f_Hp);
+  void** F = c->wf;
+  TC* D = as<TC>(F[6]);
+  TC* r = as<TC>(F[8]);
+  TC* x = as<TC>(F[10]);
+  TC* p = as<TC>(F[11]);
+  TC* Hp = as<TC>(F[12]);
   const bool jac = o.precond == 1;
   plc_stats S{};
   reset_ticket(c);
   diag<TC>(c, s_map, w, nbar, D);
   cg_init<TC>(c, u, D, r, jac);
   const double rtol2 = o.tol * o.tol;
-  const int iters = run_cg<TC>(c, x, r, p, Hp, D, jac, rtol2, o.max_cg, o.cg_chunk);
+  const int iters = run_cg<TC>(c, x, r, p, Hp, D, jac, rtol2, o.max_cg, o.cg_chunk, o.cg_chunk);
   S.cg_iters = iters;
   S.hv_count = iters;
   const DevScalars& h = *c->sc_host;
