@@ -60,6 +60,14 @@ plc::FftPlan make_plan(int n) {
     ns *= r[i];
   }
   p.nd = plc::make_fastdiv(n);
+  // FP32 transforms of these lengths use the register-resident four-step
+  // form n = f1 f2 (see fft_tile)
+  struct Pair { int n, f1, f2; };
+  const Pair fs[] = {{256, 16, 16}, {192, 16, 12}, {128, 16, 8}, {96, 12, 8}, {64, 8, 8}, {32, 8, 4}};
+  p.f1 = p.f2 = 0;
+  for (const Pair& q : fs)
+    if (q.n == n) { p.f1 = q.f1; p.f2 = q.f2; }
+  p.f1d = plc::make_fastdiv(p.f1 ? p.f1 : 2);
   return p;
 }
 

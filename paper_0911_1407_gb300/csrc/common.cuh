@@ -44,7 +44,17 @@ struct FftPlan {
   int tstep[kMaxStages];     // twiddle index step n / (ns * rad)
   unsigned ns_m[kMaxStages]; // fast-division multiplier for ns (0 when ns = 1)
   FastDiv nd;                // division by n
+  int f1, f2;                // four-step factors n = f1 f2 (0 = use the Stockham stages)
+  FastDiv f1d;               // division by f1
 };
+
+// Slot of frequency (or, after an inverse, position) k in a line left by the
+// four-step transform in transposed order; identity for the Stockham stages.
+__device__ __forceinline__ int fft_slot(const FftPlan& p, int k) {
+  if (!p.f1) return k;
+  const int q = (int)fdiv((unsigned)k, p.f1d);
+  return (k - q * p.f1) * p.f2 + q;
+}
 
 // Device-resident scalars of the solver (one instance per context).
 struct DevScalars {
@@ -175,6 +185,193 @@ __device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan&
     __syncthreads();
     cpx<T>* t = a; a = b; b = t;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident small DFTs and the four-step line FFT.
+//
+// exp(2 pi i m / R) for the radices used in registers (R in {2,3,4,6,8,12,16});
+// after unrolling m and R are constants and the switch folds away.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double unit_cos(int R, int m) {
+  const double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173;
+  const double h = 0.70710678118654752440, t = 0.86602540378443864676;
+  if (R == 16) {
+    switch (m & 15) {
+      case 0: return 1.0; case 1: return c1; case 2: return h; case 3: return s1;
+      case 4: return 0.0; case 5: return -s1; case 6: return -h; case 7: return -c1;
+      case 8: return -1.0; case 9: return -c1; case 10: return -h; case 11: return -s1;
+      case 12: return 0.0; case 13: return s1; case 14: return h; default: return c1;
+    }
+  }
+  if (R == 12) {
+    switch (m % 12) {
+      case 0: return 1.0; case 1: return t; case 2: return 0.5; case 3: return 0.0;
+      case 4: return -0.5; case 5: return -t; case 6: return -1.0; case 7: return -t;
+      case 8: return -0.5; case 9: return 0.0; case 10: return 0.5; default: return t;
+    }
+  }
+  if (R == 8) return unit_cos(16, 2 * m);
+  if (R == 6) return unit_cos(12, 2 * m);
+  if (R == 4) return unit_cos(16, 4 * m);
+  if (R == 3) return unit_cos(12, 4 * m);
+  return (m & 1) ? -1.0 : 1.0;   // R == 2
+}
+__device__ __forceinline__ double unit_sin(int R, int m) {
+  // sin(2 pi m / R) = cos(2 pi (m - R/4) / R) for R divisible by 4; the
+  // radices 6 and 3 go through 12
+  if (R == 6) return unit_sin(12, 2 * m);
+  if (R == 3) return unit_sin(12, 4 * m);
+  if (R == 2) return 0.0;
+  return unit_cos(R, ((m - R / 4) % R + R) % R);
+}
+
+// a * exp(SIGN 2 pi i m / R)
+template <typename T, int SIGN>
+__device__ __forceinline__ cpx<T> rot(cpx<T> a, int R, int m) {
+  using C = cpx<T>;
+  m %= R;
+  if (m == 0) return a;
+  if (4 * m == R) return cmul_si<SIGN>(a);
+  if (2 * m == R) return cmk<C>(-a.x, -a.y);
+  if (4 * m == 3 * R) return cmul_si<-SIGN>(a);
+  const T c = (T)unit_cos(R, m), sn = (T)SIGN * (T)unit_sin(R, m);
+  return cmk<C>(a.x * c - a.y * sn, a.x * sn + a.y * c);
+}
+
+// In-register DFT of length R (natural order in and out).  R = 6, 12, 16 are
+// done four-step as R1 x R2 (2x3, 3x4, 4x4).
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void dft_small(cpx<T>* v) {
+  using C = cpx<T>;
+  if constexpr (R == 2) Dft<T, SIGN>::r2(v);
+  else if constexpr (R == 3) Dft<T, SIGN>::r3(v);
+  else if constexpr (R == 4) Dft<T, SIGN>::r4(v);
+  else if constexpr (R == 8) Dft<T, SIGN>::r8(v);
+  else {
+    constexpr int R1 = (R == 6) ? 2 : (R == 12 ? 3 : 4);
+    constexpr int R2 = R / R1;
+    C y[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      C a[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[R2 * n1 + n2];
+      dft_small<T, SIGN, R1>(a);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) y[k1 * R2 + n2] = rot<T, SIGN>(a[k1], R, n2 * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C b[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) b[n2] = y[k1 * R2 + n2];
+      dft_small<T, SIGN, R2>(b);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+    }
+  }
+}
+
+// Four-step line FFT of length N = N1 N2 on `nl` (<= L) lines held in
+// shared memory (element i of line c at buf[i * P + c]), in place.
+// X[k1 + N1 k2] = sum_n2 W_N2^{n2 k2} W_N^{n2 k1} sum_n1 x[N2 n1 + n2] W_N1^{n1 k1}.
+// Phase A (task (c, n2)): DFT_N1 over n1, twiddle, back to the same slots
+// {m N2 + n2}; phase B (task (c, k1)): DFT_N2 over n2, back to the same slots
+// {k1 N2 + m}.  Each task rewrites exactly the slots it read, so a phase
+// needs no barrier inside; one barrier separates the phases.  The result is
+// left in transposed order: X[k1 + N1 k2] at slot k1 N2 + k2.
+// tw[m] = exp(-2 pi i m / N).  Enter after a barrier; ends with one.
+template <typename T, int SIGN, int N1, int N2>
+__device__ __forceinline__ void fft4_phase_a(cpx<T>* buf, int L, int nl, int P,
+                                             const cpx<T>* __restrict__ tw) {
+  using C = cpx<T>;
+  for (int t = threadIdx.x; t < L * N2; t += blockDim.x) {
+    const int c = t % L, n2 = t / L;
+    if (c >= nl) continue;
+    C v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = buf[(N2 * n1 + n2) * P + c];
+    dft_small<T, SIGN, N1>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      if (k1 > 0 && n2 > 0) {
+        C w = tw[n2 * k1];
+        if (SIGN > 0) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+      }
+      buf[(k1 * N2 + n2) * P + c] = v[k1];
+    }
+  }
+}
+
+template <typename T, int SIGN, int N1, int N2>
+__device__ __forceinline__ void fft4_phase_b(cpx<T>* buf, int L, int nl, int P) {
+  using C = cpx<T>;
+  for (int t = threadIdx.x; t < L * N1; t += blockDim.x) {
+    const int c = t % L, k1 = t / L;
+    if (c >= nl) continue;
+    C v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[(k1 * N2 + n2) * P + c];
+    dft_small<T, SIGN, N2>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) buf[(k1 * N2 + k2) * P + c] = v[k2];
+  }
+}
+
+template <typename T, int SIGN, int N1, int N2>
+__device__ __forceinline__ void fft4(cpx<T>* buf, int L, int nl, int P, const cpx<T>* tw) {
+  fft4_phase_a<T, SIGN, N1, N2>(buf, L, nl, P, tw);
+  __syncthreads();
+  fft4_phase_b<T, SIGN, N1, N2>(buf, L, nl, P);
+  __syncthreads();
+}
+
+// Forward transform, pointwise multiply by mul(c, k) (k = frequency index),
+// inverse transform (unnormalised), in place; the result is in natural
+// order.  The spectrum of each phase-B task stays in registers between the
+// two transforms.
+template <typename T, int N1, int N2, typename Mul>
+__device__ __forceinline__ void fft4_filter(cpx<T>* buf, int L, int nl, int P, const cpx<T>* tw,
+                                            Mul mul) {
+  using C = cpx<T>;
+  constexpr int N = N1 * N2;
+  fft4_phase_a<T, -1, N1, N2>(buf, L, nl, P, tw);
+  __syncthreads();
+  for (int t = threadIdx.x; t < L * N1; t += blockDim.x) {
+    const int c = t % L, k1 = t / L;
+    if (c >= nl) continue;
+    C v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[(k1 * N2 + n2) * P + c];
+    dft_small<T, -1, N2>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], mul(c, k1 + N1 * k2));
+    dft_small<T, +1, N2>(v);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      if (k1 > 0 && n2 > 0) {
+        C w = tw[n2 * k1];
+        w.y = -w.y;
+        v[n2] = cmul(v[n2], w);
+      }
+      buf[(k1 * N2 + n2) * P + c] = v[n2];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < L * N2; t += blockDim.x) {
+    const int c = t % L, n2 = t / L;
+    if (c >= nl) continue;
+    C v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = buf[(k1 * N2 + n2) * P + c];
+    dft_small<T, +1, N1>(v);
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) buf[(N2 * n1 + n2) * P + c] = v[n1];
+  }
+  __syncthreads();
+  (void)N;
 }
 
 // ---------------------------------------------------------------------------

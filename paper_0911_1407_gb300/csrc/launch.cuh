@@ -20,7 +20,7 @@ template <> inline const double* multiplier<double>(const plc_ctx* c) { return c
 // (n = 512) needs, once per kernel instantiation.
 template <typename T, auto Kernel> inline void set_smem() {
   static const cudaError_t once = cudaFuncSetAttribute(
-      Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeom<T>::smem_bytes(512));
+      Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassGeom<T>::smem_bytes_max(512));
   check(once, "cudaFuncSetAttribute");
 }
 
@@ -34,7 +34,7 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
   const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
                                 : (sizeof(T) == 8 ? S_XF64 : S_XF32);
   const int n = c->n, h = n / 2 + 1;
-  const size_t sm = G::smem_bytes(n);
+  const size_t sm = G::smem_bytes(c->plan);
   cpx<T>* A = static_cast<cpx<T>*>(c->specA);
   cpx<T>* B = static_cast<cpx<T>*>(c->specB);
   const cpx<T>* tw = twiddles<T>(c);

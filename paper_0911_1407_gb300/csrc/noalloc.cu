@@ -115,6 +115,8 @@ plc::FftPlan noalloc_plan(int n) {
     ns *= p.rad[i];
   }
   p.nd = plc::make_fastdiv(n);
+  p.f1 = p.f2 = 0;                    // FP64: Stockham stages
+  p.f1d = plc::make_fastdiv(2);
   return p;
 }
 
@@ -199,7 +201,7 @@ extern "C" plc_status plc_hessvec_noalloc(int n, double box, const double* k, co
   using Epi = EpiHessS<double>;
   const FftPlan plan = noalloc_plan(n);
   const int h = n / 2 + 1;
-  const size_t sm = G::smem_bytes(n);
+  const size_t sm = G::smem_bytes(plan);
   const dim3 gx((n + G::RY - 1) / G::RY, n), gy((n + G::L - 1) / G::L, h);
   const Pro pro{v};
   const Epi epi{s, w, nbar, v, Hv};

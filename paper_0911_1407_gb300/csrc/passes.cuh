@@ -34,11 +34,60 @@ template <typename T> struct PassGeom {
   static constexpr int P = L + 1;         // padded pitch of a tile row
   static constexpr int RY = 2 * L;        // real rows per x-pass tile
   static __host__ __device__ int buf_elems(int n) { return n * P; }
-  // twiddles + two ping-pong line buffers
-  static __host__ __device__ size_t smem_bytes(int n) {
+  // the four-step transform (FP32 only) works in place in one line buffer;
+  // the Stockham stages ping-pong between two
+  static __host__ __device__ bool four_step(const FftPlan& p) { return sizeof(T) == 4 && p.f1; }
+  static __host__ __device__ size_t smem_bytes(const FftPlan& p) {
+    return sizeof(cpx<T>) * ((size_t)p.n + (four_step(p) ? 1 : 2) * (size_t)buf_elems(p.n));
+  }
+  static __host__ __device__ size_t smem_bytes_max(int n) {
     return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)buf_elems(n));
   }
 };
+
+// One line transform of the tile in `a` (natural order in).  The result is
+// in `a`, in the order given by fft_slot(plan, k).
+template <typename T, int SIGN>
+__device__ __forceinline__ void fft_tile(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
+                                         const cpx<T>* tw) {
+  using G = PassGeom<T>;
+  if constexpr (sizeof(T) == 4) {
+    const int f = plan.f1 * 64 + plan.f2;
+    if (f == 16 * 64 + 16) { fft4<T, SIGN, 16, 16>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 8) { fft4<T, SIGN, 16, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 12) { fft4<T, SIGN, 16, 12>(a, G::L, nl, G::P, tw); return; }
+    if (f == 12 * 64 + 8) { fft4<T, SIGN, 12, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 8 * 64 + 8) { fft4<T, SIGN, 8, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 8 * 64 + 4) { fft4<T, SIGN, 8, 4>(a, G::L, nl, G::P, tw); return; }
+  }
+  fft_lines<T, SIGN, G::L>(a, b, plan, nl, G::P, tw);
+}
+
+// Forward transform, multiply by mul(line, kz), inverse transform: natural
+// order in and out.
+template <typename T, typename Mul>
+__device__ __forceinline__ void filter_tile(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
+                                            const cpx<T>* tw, Mul mul) {
+  using G = PassGeom<T>;
+  if constexpr (sizeof(T) == 4) {
+    const int f = plan.f1 * 64 + plan.f2;
+    if (f == 16 * 64 + 16) { fft4_filter<T, 16, 16>(a, G::L, nl, G::P, tw, mul); return; }
+    if (f == 16 * 64 + 8) { fft4_filter<T, 16, 8>(a, G::L, nl, G::P, tw, mul); return; }
+    if (f == 16 * 64 + 12) { fft4_filter<T, 16, 12>(a, G::L, nl, G::P, tw, mul); return; }
+    if (f == 12 * 64 + 8) { fft4_filter<T, 12, 8>(a, G::L, nl, G::P, tw, mul); return; }
+    if (f == 8 * 64 + 8) { fft4_filter<T, 8, 8>(a, G::L, nl, G::P, tw, mul); return; }
+    if (f == 8 * 64 + 4) { fft4_filter<T, 8, 4>(a, G::L, nl, G::P, tw, mul); return; }
+  }
+  fft_lines<T, -1, G::L>(a, b, plan, nl, G::P, tw);
+  const int n = plan.n;
+  const FastDiv ld = make_fastdiv(nl);
+  for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
+    const int kz = fdiv(e, ld), line = e - kz * nl;
+    a[kz * G::P + line] = cscale(a[kz * G::P + line], mul(line, kz));
+  }
+  __syncthreads();
+  fft_lines<T, +1, G::L>(a, b, plan, nl, G::P, tw);
+}
 
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cpx<T>* tw, const cpx<T>* __restrict__ twg, int n) {
@@ -109,12 +158,12 @@ k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ t
     }
   }
   __syncthreads();
-  fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
+  fft_tile<T, -1>(a, b, plan, lines, tw);
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < h * lines; e += kThreads) {
     const int k = fdiv(e, ld), j = e - k * lines;
-    const C zk = a[k * G::P + j];
-    const C zc = cconj(a[(k ? n - k : 0) * G::P + j]);
+    const C zk = a[fft_slot(plan, k) * G::P + j];
+    const C zc = cconj(a[fft_slot(plan, k ? n - k : 0) * G::P + j]);
     const C s = cadd(zk, zc), d = csub(zk, zc);
     st_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], cmk<C>((T)0.5 * s.x, (T)0.5 * s.y),
             cmk<C>((T)0.5 * d.y, (T)-0.5 * d.x));
@@ -140,11 +189,11 @@ k_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, FftPlan plan,
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
+  fft_tile<T, -1>(a, b, plan, lines, tw);
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = fdiv(e, ld), line = e - ky * lines;
-    B[((size_t)kx * n + ky) * n + z0 + line] = a[ky * G::P + line];
+    B[((size_t)kx * n + ky) * n + z0 + line] = a[fft_slot(plan, ky) * G::P + line];
   }
 }
 
@@ -170,19 +219,13 @@ k_z(cpx<T>* __restrict__ B, const T* __restrict__ M, int zero_dc, FftPlan plan,
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_lines<T, -1, G::L>(a, b, plan, lines, G::P, tw);
-  const FastDiv ld = make_fastdiv(lines);
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int kz = fdiv(e, ld), line = e - kz * lines;
+  auto mul = [&](int line, int kz) -> T {
     const int ky = ky0 + line;
     const int my = min(ky, n - ky), mz = min(kz, n - kz);
     const int m2 = kx * kx + my * my + mz * mz;
-    T f = __ldg(M + m2);
-    if (zero_dc && m2 == 0) f = (T)0;
-    a[kz * G::P + line] = cscale(a[kz * G::P + line], f);
-  }
-  __syncthreads();
-  fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
+    return (zero_dc && m2 == 0) ? (T)0 : __ldg(M + m2);
+  };
+  filter_tile<T>(a, b, plan, lines, tw, mul);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = fdiv(e, plan.nd), zz = e - line * n;
     B[base + e] = a[zz * G::P + line];
@@ -208,10 +251,10 @@ k_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, FftPlan plan,
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
+  fft_tile<T, +1>(a, b, plan, lines, tw);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = fdiv(e, plan.nd), y = e - line * n;
-    A[((size_t)(z0 + line) * h + kx) * n + y] = a[y * G::P + line];
+    A[((size_t)(z0 + line) * h + kx) * n + y] = a[fft_slot(plan, y) * G::P + line];
   }
 }
 
@@ -258,7 +301,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
     }
   }
   __syncthreads();
-  fft_lines<T, +1, G::L>(a, b, plan, lines, G::P, tw);
+  fft_tile<T, +1>(a, b, plan, lines, tw);
   typename Epi::Acc acc[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
   for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
@@ -266,7 +309,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
 #pragma unroll 4
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int row = fdiv(e, plan.nd), x = e - row * n;
-    const C zz = a[x * G::P + (row >> 1)];
+    const C zz = a[fft_slot(plan, x) * G::P + (row >> 1)];
     const T y = (row & 1) ? zz.y : zz.x;
     epi(((size_t)z * n + (y0 + row)) * n + x, y, acc);
   }

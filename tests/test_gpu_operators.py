@@ -143,3 +143,43 @@ def test_invalid_arguments(plc):
     N = torch.zeros((8, 8, 8), dtype=torch.int32, device="cuda")
     with pytest.raises(plc.PlcError):
         c.logpost_grad(x, N, None, -1.0)       # nbar <= 0
+
+
+_LARGE_REF = {}
+
+
+def _large_case(n):
+    """Oracle S^-1 x and H v at a production-sized grid (computed once)."""
+    if n not in _LARGE_REF:
+        box = 500.0 * n / 256
+        k, P = pk_table_for(n, box, nbins=512, seed=1)
+        inv = orc.inverse_eigenvalues(n, box, k, P, 0.0)
+        rng = np.random.default_rng(100 + n)
+        x = rng.standard_normal((n, n, n))
+        s = -1.62 + 0.8 * rng.standard_normal((n, n, n))
+        p = orc.Problem(np.zeros((n, n, n), np.int32), None, 1.0, -1.62, inv)
+        # the mixed-precision operators see s rounded to FP32
+        s32 = s.astype(np.float32).astype(np.float64)
+        _LARGE_REF[n] = dict(box=box, k=k, P=P, x=x, s=s, s32=s32,
+                             sinv=orc.apply_Sinv(x, inv),
+                             hv64=orc.hessvec(s, x, p), hv32=orc.hessvec(s32, x, p))
+    return _LARGE_REF[n]
+
+
+@pytest.mark.parametrize("n", [128, 192, 256])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_operators_at_production_sizes(plc, n, precision):
+    """Full-size grids, where the FP32 passes use the register-resident
+    four-step transforms (16x8, 16x12, 16x16) and FP64 the Stockham stages."""
+    r = _large_case(n)
+    c = plc.Context(n, r["box"], precision)
+    c.set_prior(r["k"], r["P"], -1.62)
+    y = host(c.prior_apply(dev(r["x"], c.real)))
+    s = r["s"] if precision == "fp64" else r["s32"]
+    hv = host(c.hessvec(dev(s, c.real), None, 1.0, dev(r["x"], c.real)))
+    if precision == "fp64":
+        assert np.max(np.abs(y - r["sinv"])) <= 1e-12 * np.max(np.abs(r["sinv"]))
+        assert np.max(np.abs(hv - r["hv64"])) <= 1e-12 * np.max(np.abs(r["hv64"]))
+    else:
+        assert rel_l2(y, r["sinv"]) <= 1e-5
+        assert rel_l2(hv, r["hv32"]) <= 1e-5
