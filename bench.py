@@ -227,7 +227,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["plc", "reference"], default="plc")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 solve, Hv/s sweeps and the CPU baseline")
-    ap.add_argument("--micro", choices=["hv32", "hv64", "grad32", "grad64"],
+    ap.add_argument("--micro", choices=["hv32", "hv64", "grad32", "grad64", "map32", "map64"],
                     help="profiling aid: run --reps single operator calls at size --n and exit")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--reps", type=int, default=3)
@@ -404,11 +404,15 @@ def micro(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
+    s64 = torch.empty((n,) * 3, dtype=torch.float64, device="cuda")
     for _ in range(args.reps):
         if args.micro.startswith("hv"):
             c.hessvec(s, None, 1.0, v, out)
-        else:
+        elif args.micro.startswith("grad"):
             c.logpost_grad(s, N, None, 1.0, grad=out)
+        else:
+            s64.fill_(-1.62)
+            c.newton_krylov_map(N, None, 1.0, s=s64, tol=1e-6, raise_on_fail=False)
     e1.record()
     torch.cuda.synchronize()
     print(json.dumps({"micro": args.micro, "n": n, "reps": args.reps,

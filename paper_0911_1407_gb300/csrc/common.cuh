@@ -50,8 +50,9 @@ struct FftPlan {
 
 // Slot of frequency (or, after an inverse, position) k in a line left by the
 // four-step transform in transposed order; identity for the Stockham stages.
-__device__ __forceinline__ int fft_slot(const FftPlan& p, int k) {
-  if (!p.f1) return k;
+// `four_step` says which of the two produced the line.
+__device__ __forceinline__ int fft_slot(const FftPlan& p, bool four_step, int k) {
+  if (!four_step) return k;
   const int q = (int)fdiv((unsigned)k, p.f1d);
   return (k - q * p.f1) * p.f2 + q;
 }
@@ -325,6 +326,45 @@ __device__ __forceinline__ void fft4(cpx<T>* buf, int L, int nl, int P, const cp
   fft4_phase_a<T, SIGN, N1, N2>(buf, L, nl, P, tw);
   __syncthreads();
   fft4_phase_b<T, SIGN, N1, N2>(buf, L, nl, P);
+  __syncthreads();
+}
+
+// Inverse four-step transform from the transposed order left by fft4
+// (frequency k1 + N1 k2 at slot k1 N2 + k2) to natural order, unnormalised:
+// phase B' (inverse DFT_N2 over k2, conjugate twiddle) then phase A'
+// (inverse DFT_N1 over k1).  Enter after a barrier; ends with one.
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void fft4_inverse_t(cpx<T>* buf, int L, int nl, int P,
+                                               const cpx<T>* __restrict__ tw) {
+  using C = cpx<T>;
+  for (int t = threadIdx.x; t < L * N1; t += blockDim.x) {
+    const int c = t % L, k1 = t / L;
+    if (c >= nl) continue;
+    C v[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = buf[(k1 * N2 + k2) * P + c];
+    dft_small<T, +1, N2>(v);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      if (k1 > 0 && n2 > 0) {
+        C w = tw[n2 * k1];
+        w.y = -w.y;
+        v[n2] = cmul(v[n2], w);
+      }
+      buf[(k1 * N2 + n2) * P + c] = v[n2];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < L * N2; t += blockDim.x) {
+    const int c = t % L, n2 = t / L;
+    if (c >= nl) continue;
+    C v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = buf[(k1 * N2 + n2) * P + c];
+    dft_small<T, +1, N1>(v);
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) buf[(N2 * n1 + n2) * P + c] = v[n1];
+  }
   __syncthreads();
 }
 

@@ -12,6 +12,11 @@
 
 namespace plc {
 
+// Jacobi preconditioner z = r / (D + c), the same expression wherever the CG
+// needs it (a fast reciprocal for FP32; M stays a fixed positive diagonal).
+__device__ __forceinline__ float jacobi(float r, float d, float c) { return __fdividef(r, d + c); }
+__device__ __forceinline__ double jacobi(double r, double d, double c) { return r / (d + c); }
+
 // ------------------------------- prologues --------------------------------
 template <typename T> struct ProLoad {
   const T* x;
@@ -38,7 +43,7 @@ template <typename T, bool JAC> struct ProCgDir {
   __device__ T operator()(size_t i) const {
     const T beta = (T)__ldg(&sc->beta);
     const T ri = __ldg(r + i);
-    const T zi = JAC ? ri / (__ldg(D + i) + c) : ri;
+    const T zi = JAC ? jacobi(ri, __ldg(D + i), c) : ri;
     const T pn = beta == (T)0 ? zi : zi + beta * __ldg(p + i);
     p[i] = pn;
     return pn;
@@ -122,7 +127,7 @@ template <typename T, typename TS, typename TW, typename TC> struct EpiGrad {
     acc[4].add(ni * (st < (T)0 ? -st : st));
     // r^T M^-1 r in the precision of the CG fields
     const TC gc = (TC)gi;
-    acc[5].add((T)(jac ? gc * gc / ((TC)d + (TC)c) : gc * gc));
+    acc[5].add((T)(jac ? gc * jacobi(gc, (TC)d, (TC)c) : gc * gc));
   }
 };
 
@@ -203,7 +208,7 @@ k_cg_init(const TB* __restrict__ b, const TC* __restrict__ D, TC c, TC* __restri
        i += (size_t)gridDim.x * blockDim.x) {
     const TC ri = (TC)b[i];
     r[i] = ri;
-    const TC zi = JAC ? ri / (D[i] + c) : ri;
+    const TC zi = JAC ? jacobi(ri, D[i], c) : ri;
     a0.add(ri * zi);
     a1.add(ri * ri);
   }
@@ -247,7 +252,7 @@ k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
     x[i] = xn;
     const TC ri = r[i] - alpha * Hp[i];
     r[i] = ri;
-    const TC zi = JAC ? ri / (D[i] + c) : ri;
+    const TC zi = JAC ? jacobi(ri, D[i], c) : ri;
     a0.add(ri * zi);
     a1.add(ri * ri);
     a2.max(xn < (TC)0 ? -xn : xn);
@@ -310,7 +315,7 @@ k_newton_update(const T* __restrict__ s, const T* __restrict__ y, const T* __res
     acc[3].add(ni * sn);
     acc[4].add(ni * (sn < (T)0 ? -sn : sn));
     const TC gc = (TC)gn;
-    acc[5].add((T)(jac ? gc * gc / ((TC)d + (TC)c) : gc * gc));
+    acc[5].add((T)(jac ? gc * jacobi(gc, (TC)d, (TC)c) : gc * gc));
   }
   double tot[6];
 #pragma unroll

@@ -45,22 +45,40 @@ template <typename T> struct PassGeom {
   }
 };
 
-// One line transform of the tile in `a` (natural order in).  The result is
-// in `a`, in the order given by fft_slot(plan, k).
-template <typename T, int SIGN>
-__device__ __forceinline__ void fft_tile(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
-                                         const cpx<T>* tw) {
+// Forward line transform of the tile in `a`: natural order in; the result is
+// in `a` with frequency k at slot fft_slot(plan, four_step, k).
+template <typename T>
+__device__ __forceinline__ void fft_tile_fwd(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
+                                             const cpx<T>* tw) {
   using G = PassGeom<T>;
   if constexpr (sizeof(T) == 4) {
     const int f = plan.f1 * 64 + plan.f2;
-    if (f == 16 * 64 + 16) { fft4<T, SIGN, 16, 16>(a, G::L, nl, G::P, tw); return; }
-    if (f == 16 * 64 + 8) { fft4<T, SIGN, 16, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 16 * 64 + 12) { fft4<T, SIGN, 16, 12>(a, G::L, nl, G::P, tw); return; }
-    if (f == 12 * 64 + 8) { fft4<T, SIGN, 12, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 8 * 64 + 8) { fft4<T, SIGN, 8, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 8 * 64 + 4) { fft4<T, SIGN, 8, 4>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 16) { fft4<T, -1, 16, 16>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 8) { fft4<T, -1, 16, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 12) { fft4<T, -1, 16, 12>(a, G::L, nl, G::P, tw); return; }
+    if (f == 12 * 64 + 8) { fft4<T, -1, 12, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 8 * 64 + 8) { fft4<T, -1, 8, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 8 * 64 + 4) { fft4<T, -1, 8, 4>(a, G::L, nl, G::P, tw); return; }
   }
-  fft_lines<T, SIGN, G::L>(a, b, plan, nl, G::P, tw);
+  fft_lines<T, -1, G::L>(a, b, plan, nl, G::P, tw);
+}
+
+// Inverse line transform (unnormalised): frequency k at slot
+// fft_slot(plan, four_step, k) in; natural order out, in `a`.
+template <typename T>
+__device__ __forceinline__ void fft_tile_inv(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
+                                             const cpx<T>* tw) {
+  using G = PassGeom<T>;
+  if constexpr (sizeof(T) == 4) {
+    const int f = plan.f1 * 64 + plan.f2;
+    if (f == 16 * 64 + 16) { fft4_inverse_t<T, 16, 16>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 8) { fft4_inverse_t<T, 16, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 16 * 64 + 12) { fft4_inverse_t<T, 16, 12>(a, G::L, nl, G::P, tw); return; }
+    if (f == 12 * 64 + 8) { fft4_inverse_t<T, 12, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 8 * 64 + 8) { fft4_inverse_t<T, 8, 8>(a, G::L, nl, G::P, tw); return; }
+    if (f == 8 * 64 + 4) { fft4_inverse_t<T, 8, 4>(a, G::L, nl, G::P, tw); return; }
+  }
+  fft_lines<T, +1, G::L>(a, b, plan, nl, G::P, tw);
 }
 
 // Forward transform, multiply by mul(line, kz), inverse transform: natural
@@ -158,12 +176,12 @@ k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ t
     }
   }
   __syncthreads();
-  fft_tile<T, -1>(a, b, plan, lines, tw);
+  fft_tile_fwd<T>(a, b, plan, lines, tw);
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < h * lines; e += kThreads) {
     const int k = fdiv(e, ld), j = e - k * lines;
-    const C zk = a[fft_slot(plan, k) * G::P + j];
-    const C zc = cconj(a[fft_slot(plan, k ? n - k : 0) * G::P + j]);
+    const C zk = a[fft_slot(plan, G::four_step(plan), k) * G::P + j];
+    const C zc = cconj(a[fft_slot(plan, G::four_step(plan), k ? n - k : 0) * G::P + j]);
     const C s = cadd(zk, zc), d = csub(zk, zc);
     st_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], cmk<C>((T)0.5 * s.x, (T)0.5 * s.y),
             cmk<C>((T)0.5 * d.y, (T)-0.5 * d.x));
@@ -189,11 +207,11 @@ k_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, FftPlan plan,
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_tile<T, -1>(a, b, plan, lines, tw);
+  fft_tile_fwd<T>(a, b, plan, lines, tw);
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = fdiv(e, ld), line = e - ky * lines;
-    B[((size_t)kx * n + ky) * n + z0 + line] = a[fft_slot(plan, ky) * G::P + line];
+    B[((size_t)kx * n + ky) * n + z0 + line] = a[fft_slot(plan, G::four_step(plan), ky) * G::P + line];
   }
 }
 
@@ -247,14 +265,15 @@ k_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, FftPlan plan,
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = fdiv(e, ld), line = e - ky * lines;
-    cp_async(&a[ky * G::P + line], &B[((size_t)kx * n + ky) * n + z0 + line]);
+    cp_async(&a[fft_slot(plan, G::four_step(plan), ky) * G::P + line],
+             &B[((size_t)kx * n + ky) * n + z0 + line]);
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_tile<T, +1>(a, b, plan, lines, tw);
+  fft_tile_inv<T>(a, b, plan, lines, tw);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int line = fdiv(e, plan.nd), y = e - line * n;
-    A[((size_t)(z0 + line) * h + kx) * n + y] = a[fft_slot(plan, y) * G::P + line];
+    A[((size_t)(z0 + line) * h + kx) * n + y] = a[y * G::P + line];
   }
 }
 
@@ -277,6 +296,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
   const int lines = rows >> 1;
   const int npairs = h * lines;
   const FastDiv ld = make_fastdiv(lines);
+  const bool fs = G::four_step(plan);
   constexpr int B4 = 4;
   for (int base = threadIdx.x; base < npairs; base += B4 * kThreads) {
     C xa[B4], xb[B4];
@@ -295,13 +315,14 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
         const int k = fdiv(e, ld), j = e - k * lines;
         C va = xa[q], vb = xb[q];
         if (k == 0 || k == nh) { va.y = (T)0; vb.y = (T)0; }
-        a[k * G::P + j] = cmk<C>(va.x - vb.y, va.y + vb.x);
-        if (k > 0 && k < nh) a[(n - k) * G::P + j] = cmk<C>(va.x + vb.y, vb.x - va.y);
+        a[fft_slot(plan, fs, k) * G::P + j] = cmk<C>(va.x - vb.y, va.y + vb.x);
+        if (k > 0 && k < nh)
+          a[fft_slot(plan, fs, n - k) * G::P + j] = cmk<C>(va.x + vb.y, vb.x - va.y);
       }
     }
   }
   __syncthreads();
-  fft_tile<T, +1>(a, b, plan, lines, tw);
+  fft_tile_inv<T>(a, b, plan, lines, tw);
   typename Epi::Acc acc[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
   for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
@@ -309,7 +330,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
 #pragma unroll 4
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int row = fdiv(e, plan.nd), x = e - row * n;
-    const C zz = a[fft_slot(plan, x) * G::P + (row >> 1)];
+    const C zz = a[x * G::P + (row >> 1)];
     const T y = (row & 1) ? zz.y : zz.x;
     epi(((size_t)z * n + (y0 + row)) * n + x, y, acc);
   }
