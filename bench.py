@@ -465,6 +465,22 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
                                                   "grad_ffts", "grad_rel")}
     line["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()),
                              "rel_l2": float(d.norm() / s64.norm())}
+    # the FP32 -> FP64 switch point of the mixed solve
+    sweep = {}
+    sm = torch.empty_like(s64)
+    for sw in (1e-3, 1e-4, 1e-5):
+        for rep in range(2):
+            sm.fill_(m.mu)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rs = ctx.newton_krylov_map(N_dev, None, m.nbar, s=sm, tol=TOL, mixed_switch=sw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        dd = sm - s64
+        sweep[f"{sw:g}"] = {"ms": e0.elapsed_time(e1), "newton": rs.stats["newton_iters"],
+                            "cg": rs.stats["cg_iters"], "grad_rel": rs.stats["grad_rel"],
+                            "max_abs_vs_fp64": float(dd.abs().max())}
+    line["mixed_switch_sweep"] = sweep
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:
         t_hv, t_g = time_oracle_sample(m)

@@ -18,8 +18,10 @@ __device__ __forceinline__ float jacobi(float r, float d, float c) { return __fd
 __device__ __forceinline__ double jacobi(double r, double d, double c) { return r / (d + c); }
 
 // ------------------------------- prologues --------------------------------
+// Every prologue has prepare(), run once per block before the element loop.
 template <typename T> struct ProLoad {
   const T* x;
+  __device__ void prepare() {}
   __device__ T operator()(size_t i) const { return __ldg(x + i); }
 };
 
@@ -28,6 +30,7 @@ template <typename T> struct ProLoad {
 template <typename T, typename TS> struct ProShift {
   const TS* s;
   double mu;
+  __device__ void prepare() {}
   // difference taken in the transform precision (no FP64 work for float)
   __device__ T operator()(size_t i) const { return (T)__ldg(s + i) - (T)mu; }
 };
@@ -40,8 +43,9 @@ template <typename T, bool JAC> struct ProCgDir {
   T c;                 // (S^-1)_ii, the prior's share of diag(H)
   T* p;
   const DevScalars* sc;
+  T beta;              // loaded by prepare()
+  __device__ void prepare() { beta = (T)__ldg(&sc->beta); }
   __device__ T operator()(size_t i) const {
-    const T beta = (T)__ldg(&sc->beta);
     const T ri = __ldg(r + i);
     const T zi = JAC ? jacobi(ri, __ldg(D + i), c) : ri;
     const T pn = beta == (T)0 ? zi : zi + beta * __ldg(p + i);
@@ -195,6 +199,31 @@ struct FinAlpha {
   }
 };
 
+// ------------------------- 4-wide element access ---------------------------
+// Element-wise kernels move four consecutive elements per thread and step
+// with 16-byte loads (n^3 is a multiple of 8; fields are 16-byte aligned).
+template <typename T> struct V4 { T v[4]; };
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return V4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ V4<int32_t> ld4(const int32_t* p) {
+  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+  return V4<int32_t>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& a) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
+}
+
 // ------------------------------ CG kernels --------------------------------
 // Start CG on H x = b from x = 0: r = b, rz = r^T M^-1 r, rr = r^T r.
 template <typename TC, typename TB, bool JAC>
@@ -246,16 +275,25 @@ k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
   a0.init(false);
   a1.init(false);
   a2.init(true);
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const TC xn = first ? alpha * p[i] : x[i] + alpha * p[i];
-    x[i] = xn;
-    const TC ri = r[i] - alpha * Hp[i];
-    r[i] = ri;
-    const TC zi = JAC ? jacobi(ri, D[i], c) : ri;
-    a0.add(ri * zi);
-    a1.add(ri * ri);
-    a2.max(xn < (TC)0 ? -xn : xn);
+  const size_t step = (size_t)gridDim.x * blockDim.x * 4;
+#pragma unroll 2
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < n3; i += step) {
+    const V4<TC> pv = ld4(p + i), hv = ld4(Hp + i), dv = ld4(D + i);
+    V4<TC> xv = first ? V4<TC>{} : ld4(x + i);
+    V4<TC> rv = ld4(r + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const TC xn = first ? alpha * pv.v[j] : xv.v[j] + alpha * pv.v[j];
+      xv.v[j] = xn;
+      const TC ri = rv.v[j] - alpha * hv.v[j];
+      rv.v[j] = ri;
+      const TC zi = JAC ? jacobi(ri, dv.v[j], c) : ri;
+      a0.add(ri * zi);
+      a1.add(ri * ri);
+      a2.max(xn < (TC)0 ? -xn : xn);
+    }
+    st4(x + i, xv);
+    st4(r + i, rv);
   }
   double acc[3] = {a0.get(), a1.get(), a2.get()};
   struct Fin {
@@ -293,29 +331,45 @@ k_newton_update(const T* __restrict__ s, const T* __restrict__ y, const T* __res
   Acc acc[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) acc[j].init(false);
-  const T tt = (T)tau;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const TC xi_i = xi[i];
-    const TC b_i = (TC)(-g[i]);
-    const TC sinv_xi = b_i - r[i] - D[i] * xi_i;
-    const T yn = y[i] + tt * (T)sinv_xi;
-    const T sn = s[i] + tt * (T)xi_i;
-    const T d = (T)nbar * (w ? (T)w[i] : (T)1) * exp(sn);
-    const T ni = (T)N[i];
-    const T gn = yn + d - ni;
-    s2[i] = sn;
-    y2[i] = yn;
-    g2[i] = gn;
-    D2[i] = (TC)d;
-    r2[i] = (TC)(-gn);
-    acc[0].add((sn - (T)mu) * yn);
-    acc[1].add(d - ni * sn);
-    acc[2].add(gn * gn);
-    acc[3].add(ni * sn);
-    acc[4].add(ni * (sn < (T)0 ? -sn : sn));
-    const TC gc = (TC)gn;
-    acc[5].add((T)(jac ? gc * jacobi(gc, (TC)d, (TC)c) : gc * gc));
+  const T tt = (T)tau, nb = (T)nbar, m = (T)mu;
+  const TC cc = (TC)c;
+  const size_t step = (size_t)gridDim.x * blockDim.x * 4;
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < n3; i += step) {
+    const V4<TC> xv = ld4(xi + i), rv = ld4(r + i), dv = ld4(D + i);
+    const V4<T> sv = ld4(s + i), yv = ld4(y + i), gv = ld4(g + i);
+    const V4<int32_t> nv = ld4(N + i);
+    V4<double> wv{{1.0, 1.0, 1.0, 1.0}};
+    if (w) wv = ld4(w + i);
+    V4<T> so, yo, go;
+    V4<TC> dout, rout;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const TC b_j = (TC)(-gv.v[j]);
+      const TC sinv_xi = b_j - rv.v[j] - dv.v[j] * xv.v[j];
+      const T yn = yv.v[j] + tt * (T)sinv_xi;
+      const T sn = sv.v[j] + tt * (T)xv.v[j];
+      const T d = nb * (T)wv.v[j] * exp(sn);
+      const T ni = (T)nv.v[j];
+      const T gn = yn + d - ni;
+      so.v[j] = sn;
+      yo.v[j] = yn;
+      go.v[j] = gn;
+      dout.v[j] = (TC)d;
+      rout.v[j] = (TC)(-gn);
+      acc[0].add((sn - m) * yn);
+      acc[1].add(d - ni * sn);
+      acc[2].add(gn * gn);
+      const TC nc = (TC)nv.v[j], sc = (TC)sn;
+      acc[3].add((T)(nc * sc));
+      acc[4].add((T)(nc * (sc < (TC)0 ? -sc : sc)));
+      const TC gc = (TC)gn;
+      acc[5].add((T)(jac ? gc * jacobi(gc, (TC)d, cc) : gc * gc));
+    }
+    st4(s2 + i, so);
+    st4(y2 + i, yo);
+    st4(g2 + i, go);
+    st4(D2 + i, dout);
+    st4(r2 + i, rout);
   }
   double tot[6];
 #pragma unroll

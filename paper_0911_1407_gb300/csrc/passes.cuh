@@ -150,12 +150,13 @@ __global__ void __launch_bounds__(kThreads)
 k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ twg,
      const int* __restrict__ done) {
   PLC_PASS_PROLOGUE;
+  pro.prepare();
   const int n = plan.n, h = n / 2 + 1;
   const int z = blockIdx.y, y0 = blockIdx.x * G::RY;
   const int rows = min(G::RY, n - y0);
   const int lines = rows >> 1;
   const int total = rows * n;
-  constexpr int B8 = 8;
+  constexpr int B8 = 16;
   for (int base = threadIdx.x; base < total; base += B8 * kThreads) {
     T u[B8];
 #pragma unroll
