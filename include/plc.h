@@ -108,7 +108,7 @@ typedef struct {
   double eta_max;      /* CG forcing term cap (default 0.5) */
   int cg_chunk;        /* CG iterations enqueued between host checks (default 8) */
   double mixed_switch; /* PLC_MIXED: gradients in FP32 while ||g|| / ||g0|| is at or
-                          above this, in FP64 below it (default 1e-3; >= 1 means FP64
+                          above this, in FP64 below it (default 1e-4; >= 1 means FP64
                           throughout).  The stopping test is always taken in FP64. */
 } plc_opts;
 

@@ -12,6 +12,31 @@
 
 namespace plc {
 
+// ------------------------- 4-wide element access ---------------------------
+// Element-wise kernels move four consecutive elements per thread and step
+// with 16-byte loads (n^3 is a multiple of 8; fields are 16-byte aligned).
+template <typename T> struct V4 { T v[4]; };
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return V4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ V4<int32_t> ld4(const int32_t* p) {
+  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+  return V4<int32_t>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& a) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
+}
+
 // Jacobi preconditioner z = r / (D + c), the same expression wherever the CG
 // needs it (a fast reciprocal for FP32; M stays a fixed positive diagonal).
 __device__ __forceinline__ float jacobi(float r, float d, float c) { return __fdividef(r, d + c); }
@@ -19,10 +44,12 @@ __device__ __forceinline__ double jacobi(double r, double d, double c) { return 
 
 // ------------------------------- prologues --------------------------------
 // Every prologue has prepare(), run once per block before the element loop.
+// vec4(i) handles the four consecutive elements i .. i+3 (i a multiple of 4).
 template <typename T> struct ProLoad {
   const T* x;
   __device__ void prepare() {}
   __device__ T operator()(size_t i) const { return __ldg(x + i); }
+  __device__ V4<T> vec4(size_t i) const { return ld4(x + i); }
 };
 
 // s - mu: the prior term of the gradient (Sec. 2.3, Eq. priorlog).  s may be
@@ -33,6 +60,13 @@ template <typename T, typename TS> struct ProShift {
   __device__ void prepare() {}
   // difference taken in the transform precision (no FP64 work for float)
   __device__ T operator()(size_t i) const { return (T)__ldg(s + i) - (T)mu; }
+  __device__ V4<T> vec4(size_t i) const {
+    const V4<TS> a = ld4(s + i);
+    V4<T> o;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o.v[j] = (T)a.v[j] - (T)mu;
+    return o;
+  }
 };
 
 // CG search direction p <- M^-1 r + beta p (beta from the device scalars;
@@ -52,6 +86,19 @@ template <typename T, bool JAC> struct ProCgDir {
     p[i] = pn;
     return pn;
   }
+  __device__ V4<T> vec4(size_t i) const {
+    const V4<T> rv = ld4(r + i);
+    V4<T> dv, pv, o;
+    if (JAC) dv = ld4(D + i);
+    if (beta != (T)0) pv = ld4(p + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T zi = JAC ? jacobi(rv.v[j], dv.v[j], c) : rv.v[j];
+      o.v[j] = beta == (T)0 ? zi : zi + beta * pv.v[j];
+    }
+    st4(p + i, o);
+    return o;
+  }
 };
 
 // ------------------------------- epilogues --------------------------------
@@ -61,6 +108,7 @@ template <typename T> struct EpiStore {
   using Acc = AccD;
   T* out;
   __device__ void operator()(size_t i, T y, Acc*) const { out[i] = y; }
+  __device__ void vec4(size_t i, const V4<T>& y, Acc*) const { st4(out + i, y); }
 };
 
 // H v = S^-1 v + nbar w e^s v (Sec. 3.1.2) with the diagonal computed here.
@@ -77,6 +125,14 @@ template <typename T> struct EpiHessS {
     const T d = nbar * (w ? __ldg(w + i) : (T)1) * exp(__ldg(s + i));
     out[i] = y + d * __ldg(v + i);
   }
+  __device__ void vec4(size_t i, const V4<T>& y, Acc*) const {
+    const V4<T> sv = ld4(s + i), vv = ld4(v + i);
+    V4<T> wv{{(T)1, (T)1, (T)1, (T)1}}, o;
+    if (w) wv = ld4(w + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o.v[j] = y.v[j] + nbar * wv.v[j] * exp(sv.v[j]) * vv.v[j];
+    st4(out + i, o);
+  }
 };
 
 // CG product H p = S^-1 p + D p, accumulating p^T H p.
@@ -92,6 +148,16 @@ template <typename T> struct EpiHessD {
     const T hv = y + __ldg(D + i) * vi;
     out[i] = hv;
     acc[0].add(vi * hv);
+  }
+  __device__ void vec4(size_t i, const V4<T>& y, Acc* acc) const {
+    const V4<T> vv = ld4(v + i), dv = ld4(D + i);
+    V4<T> o;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      o.v[j] = y.v[j] + dv.v[j] * vv.v[j];
+      acc[0].add(vv.v[j] * o.v[j]);
+    }
+    st4(out + i, o);
   }
 };
 
@@ -115,15 +181,10 @@ template <typename T, typename TS, typename TW, typename TC> struct EpiGrad {
   TC* r;                // may be null
   double c;             // Jacobi constant (S^-1)_ii
   int jac;
-  __device__ void operator()(size_t i, T y, Acc* acc) const {
-    const T st = (T)__ldg(s + i);
-    const T d = (T)nbar * (w ? (T)__ldg(w + i) : (T)1) * exp(st);
-    const T ni = (T)__ldg(N + i);
-    const T gi = y + d - ni;
-    if (yout) yout[i] = y;
-    if (g) g[i] = gi;
-    if (D) D[i] = (TC)d;
-    if (r) r[i] = (TC)(-gi);
+  // one cell: returns g and d, accumulates the sums
+  __device__ __forceinline__ void cell(T st, T wt, T ni, T y, Acc* acc, T& gi, T& d) const {
+    d = (T)nbar * wt * exp(st);
+    gi = y + d - ni;
     acc[0].add((st - (T)mu) * y);
     acc[1].add(d - ni * st);
     acc[2].add(gi * gi);
@@ -132,6 +193,34 @@ template <typename T, typename TS, typename TW, typename TC> struct EpiGrad {
     // r^T M^-1 r in the precision of the CG fields
     const TC gc = (TC)gi;
     acc[5].add((T)(jac ? gc * jacobi(gc, (TC)d, (TC)c) : gc * gc));
+  }
+  __device__ void operator()(size_t i, T y, Acc* acc) const {
+    T gi, d;
+    cell((T)__ldg(s + i), w ? (T)__ldg(w + i) : (T)1, (T)__ldg(N + i), y, acc, gi, d);
+    if (yout) yout[i] = y;
+    if (g) g[i] = gi;
+    if (D) D[i] = (TC)d;
+    if (r) r[i] = (TC)(-gi);
+  }
+  __device__ void vec4(size_t i, const V4<T>& y, Acc* acc) const {
+    const V4<TS> sv = ld4(s + i);
+    const V4<int32_t> nv = ld4(N + i);
+    V4<TW> wv{{(TW)1, (TW)1, (TW)1, (TW)1}};
+    if (w) wv = ld4(w + i);
+    V4<T> gv;
+    V4<TC> dv, rv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      T gi, d;
+      cell((T)sv.v[j], (T)wv.v[j], (T)nv.v[j], y.v[j], acc, gi, d);
+      gv.v[j] = gi;
+      dv.v[j] = (TC)d;
+      rv.v[j] = (TC)(-gi);
+    }
+    if (yout) st4(yout + i, y);
+    if (g) st4(g + i, gv);
+    if (D) st4(D + i, dv);
+    if (r) st4(r + i, rv);
   }
 };
 
@@ -143,6 +232,11 @@ template <typename T, typename TL> struct EpiDot {
   using Acc = AccD;
   __device__ void operator()(size_t i, T y, Acc* acc) const {
     acc[0].add((double)__ldg(lam + i) * (double)y);
+  }
+  __device__ void vec4(size_t i, const V4<T>& y, Acc* acc) const {
+    const V4<TL> lv = ld4(lam + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[0].add((double)lv.v[j] * (double)y.v[j]);
   }
 };
 
@@ -198,31 +292,6 @@ struct FinAlpha {
     }
   }
 };
-
-// ------------------------- 4-wide element access ---------------------------
-// Element-wise kernels move four consecutive elements per thread and step
-// with 16-byte loads (n^3 is a multiple of 8; fields are 16-byte aligned).
-template <typename T> struct V4 { T v[4]; };
-__device__ __forceinline__ V4<float> ld4(const float* p) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  return V4<float>{{a.x, a.y, a.z, a.w}};
-}
-__device__ __forceinline__ V4<double> ld4(const double* p) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  return V4<double>{{a.x, a.y, b.x, b.y}};
-}
-__device__ __forceinline__ V4<int32_t> ld4(const int32_t* p) {
-  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
-  return V4<int32_t>{{a.x, a.y, a.z, a.w}};
-}
-__device__ __forceinline__ void st4(float* p, const V4<float>& a) {
-  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
-}
-__device__ __forceinline__ void st4(double* p, const V4<double>& a) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
-}
 
 // ------------------------------ CG kernels --------------------------------
 // Start CG on H x = b from x = 0: r = b, rz = r^T M^-1 r, rr = r^T r.

@@ -155,24 +155,34 @@ k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ t
   const int z = blockIdx.y, y0 = blockIdx.x * G::RY;
   const int rows = min(G::RY, n - y0);
   const int lines = rows >> 1;
-  const int total = rows * n;
-  constexpr int B8 = 16;
-  for (int base = threadIdx.x; base < total; base += B8 * kThreads) {
-    T u[B8];
+  if (n & 3) {   // rows not a multiple of 4 long: one element per step
+    for (int e = threadIdx.x; e < rows * n; e += kThreads) {
+      const int row = fdiv(e, plan.nd), x = e - row * n;
+      reinterpret_cast<T*>(&a[x * G::P + (row >> 1)])[row & 1] =
+          pro(((size_t)z * n + (y0 + row)) * n + x);
+    }
+  }
+  // four consecutive x per thread and step: 16-byte global accesses
+  const int total4 = (n & 3) ? 0 : (rows * n) >> 2;
+  constexpr int B = 4;
+  for (int base = threadIdx.x; base < total4; base += B * kThreads) {
+    V4<T> u[B];
 #pragma unroll
-    for (int k = 0; k < B8; ++k) {
+    for (int k = 0; k < B; ++k) {
       const int e = base + k * kThreads;
-      if (e < total) {
-        const int row = fdiv(e, plan.nd), x = e - row * n;
-        u[k] = pro(((size_t)z * n + (y0 + row)) * n + x);
+      if (e < total4) {
+        const int row = fdiv(4 * e, plan.nd), x = 4 * e - row * n;
+        u[k] = pro.vec4(((size_t)z * n + (y0 + row)) * n + x);
       }
     }
 #pragma unroll
-    for (int k = 0; k < B8; ++k) {
+    for (int k = 0; k < B; ++k) {
       const int e = base + k * kThreads;
-      if (e < total) {
-        const int row = fdiv(e, plan.nd), x = e - row * n;
-        reinterpret_cast<T*>(&a[x * G::P + (row >> 1)])[row & 1] = u[k];
+      if (e < total4) {
+        const int row = fdiv(4 * e, plan.nd), x = 4 * e - row * n;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          reinterpret_cast<T*>(&a[(x + j) * G::P + (row >> 1)])[row & 1] = u[k].v[j];
       }
     }
   }
@@ -327,13 +337,24 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
   typename Epi::Acc acc[Epi::NV > 0 ? Epi::NV : 1];
 #pragma unroll
   for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
-  const int total = rows * n;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    const int row = fdiv(e, plan.nd), x = e - row * n;
-    const C zz = a[x * G::P + (row >> 1)];
-    const T y = (row & 1) ? zz.y : zz.x;
-    epi(((size_t)z * n + (y0 + row)) * n + x, y, acc);
+  if (n & 3) {   // rows not a multiple of 4 long: one element per step
+    for (int e = threadIdx.x; e < rows * n; e += kThreads) {
+      const int row = fdiv(e, plan.nd), x = e - row * n;
+      const C zz = a[x * G::P + (row >> 1)];
+      epi(((size_t)z * n + (y0 + row)) * n + x, (row & 1) ? zz.y : zz.x, acc);
+    }
+  }
+  const int total4 = (n & 3) ? 0 : (rows * n) >> 2;
+#pragma unroll 2
+  for (int e = threadIdx.x; e < total4; e += kThreads) {
+    const int row = fdiv(4 * e, plan.nd), x = 4 * e - row * n;
+    V4<T> y;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const C zz = a[(x + j) * G::P + (row >> 1)];
+      y.v[j] = (row & 1) ? zz.y : zz.x;
+    }
+    epi.vec4(((size_t)z * n + (y0 + row)) * n + x, y, acc);
   }
   if constexpr (Epi::NV > 0) {
     double tot[Epi::NV];

@@ -1,9 +1,11 @@
 """GPU parity of the operators against the FP64 oracle (through the C ABI).
 
 Sizes span several tiles and a ragged tail: tiles are 8 (FP64) / 16 (FP32)
-complex lines and 16 / 32 real rows, so n = 24, 40-free sizes like 48 and 96
-leave partial tiles along z, y and the n/2+1 kx lines; n = 4 and 6 are
-smaller than one tile.  FP64 bar: relative error <= 1e-12 (an FFT round trip
+complex lines and 16 / 32 real rows, so n = 24, 48 and 96 leave partial
+tiles along z, y and the n/2+1 kx lines; n = 4 and 6 are smaller than one
+tile; n = 6, 18 and 54 (one factor of 2) take the one-element-per-step x
+passes, the others the 4-wide ones; n = 32, 64, 96, 128, 192, 256 use the
+four-step FP32 transforms.  FP64 bar: relative error <= 1e-12 (an FFT round trip
 of length n^3 in double accumulates a few 1e-15 per stage).  FP32 bar
 (PLC_MIXED operators): relative L2 <= 1e-5, from eps32 = 6e-8 times the
 ~log2(n^3) <= 27 butterfly stages of the two transforms and the pointwise
@@ -20,7 +22,7 @@ from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock, pk_table_f
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [4, 6, 8, 12, 24, 48, 96]
+SIZES = [4, 6, 8, 12, 18, 24, 48, 54, 96]
 
 
 @pytest.fixture(scope="module")
