@@ -25,16 +25,19 @@ template <typename T> using cpx = typename CplxOf<T>::type;
 // Lines per shared-memory tile: 128 bytes of complex values per tile row.
 template <typename T> struct Tile { static constexpr int L = 128 / (2 * (int)sizeof(T)); };
 
-// Division by a runtime divisor d >= 2 as one multiply-high:
+// Division by a runtime divisor d >= 1 as one multiply-high:
 // q = umulhi(x, m) with m = ceil(2^32 / d) equals floor(x / d) whenever
-// x * d < 2^32 (here x < 2^16 and d <= 512).
+// x * d < 2^32 (here x < 2^16 and d <= 512).  d = 1 has no 32-bit m and is
+// passed through.
 struct FastDiv {
   unsigned d, m;
 };
 inline __host__ __device__ FastDiv make_fastdiv(unsigned d) {
-  return FastDiv{d, (unsigned)((0x100000000ull + d - 1) / d)};
+  return FastDiv{d, d > 1 ? (unsigned)((0x100000000ull + d - 1) / d) : 0u};
 }
-__device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) { return __umulhi(x, f.m); }
+__device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) {
+  return f.d > 1 ? __umulhi(x, f.m) : x;
+}
 
 struct FftPlan {
   int n;                     // transform length (the grid side)
