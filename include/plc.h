@@ -105,11 +105,14 @@ typedef struct {
   int precond;         /* 0 none, 1 Jacobi diag(H) (default 1) */
   double g0_norm;      /* > 0: use as ||g0|| (resume); 0: ||g(s_in)|| */
   double step_cap;     /* max |tau xi| per Newton step (default 2) */
-  double eta_max;      /* CG forcing term cap (default 0.5) */
+  double eta_max;      /* CG forcing term cap (default 0.5); the CG stops at
+                          eta = min(eta_max, max(sqrt(rel), 0.3 tol / rel)) */
   int cg_chunk;        /* CG iterations enqueued between host checks (default 8) */
   double mixed_switch; /* PLC_MIXED: gradients in FP32 while ||g|| / ||g0|| is at or
-                          above this, in FP64 below it (default 1e-4; >= 1 means FP64
-                          throughout).  The stopping test is always taken in FP64. */
+                          above this and above tol, in FP64 below it (default 1e-6;
+                          >= 1 means FP64 throughout).  The switch also happens when
+                          an FP32 Newton step below 1e-3 fails to halve ||g||.  The
+                          stopping test is always taken on an FP64 gradient. */
 } plc_opts;
 
 typedef struct {

@@ -203,10 +203,11 @@ def newton_krylov_map(p: Problem, s0: Optional[np.ndarray] = None,
     Sec. 3.1: x^{j+1} = x^j + tau^j xi^j with tau from Eq. (New5),
     tau = -xi^T grad Q / (xi^T H xi).  The paper leaves the search vector xi to
     earlier work; here xi solves H xi = -g by Jacobi-preconditioned CG to a
-    relative residual eta = min(0.5, sqrt(||g|| / ||g0||)).  The step is capped
-    so that max |tau xi| <= step_cap, then halved until the Armijo condition
-    L(s + tau xi) <= L(s) + c tau xi^T g holds (or the predicted decrease is
-    below the rounding level of L).  Stops when ||g|| / ||g0|| < tol, with
+    relative residual eta = min(0.5, max(sqrt(rel), 0.3 tol / rel)),
+    rel = ||g|| / ||g0|| (superlinear, without solving past what the stop
+    test needs).  The step is capped so that max |tau xi| <= step_cap, then
+    halved until the Armijo condition L(s + tau xi) <= L(s) + c tau xi^T g
+    holds (or the predicted decrease is below the rounding level of L).  Stops when ||g|| / ||g0|| < tol, with
     g0 = g(s0) unless g0_norm is given.  s0 defaults to mu.
     """
     shape = p.N.shape
@@ -224,7 +225,7 @@ def newton_krylov_map(p: Problem, s0: Optional[np.ndarray] = None,
             return MapResult(s, True, it, cg_total, rel, f, g0, hist)
         if it >= max_newton:
             return MapResult(s, False, it, cg_total, rel, f, g0, hist)
-        eta = min(0.5, math.sqrt(rel))
+        eta = min(0.5, max(math.sqrt(rel), 0.3 * tol / rel))
         mdiag = jacobi_diagonal(s, p)
         cg = pcg(lambda v: hessvec(s, v, p), -g, mdiag, eta, max_cg)
         cg_total += cg.iters

@@ -177,7 +177,7 @@ plc_status plc_default_opts(plc_opts* o) {
   o->step_cap = 2.0;
   o->eta_max = 0.5;
   o->cg_chunk = 8;
-  o->mixed_switch = 1e-4;
+  o->mixed_switch = 1e-6;
   return PLC_OK;
 }
 

@@ -21,7 +21,8 @@ enum Site {
   // pipelines of the Newton gradient (and line-search trials)
   S_GXF64, S_GYF64, S_GZ64, S_GYI64, S_GXI64,
   S_GXF32, S_GYF32, S_GZ32, S_GYI32, S_GXI32,
-  S_CG_INIT, S_CG_UPDATE, S_NEWTON_UPDATE, S_DIAG, S_CONVERT, S_SETUP,
+  S_CG_INIT, S_CG_UPDATE64, S_CG_UPDATE32, S_NEWTON_UPDATE64, S_NEWTON_UPDATE32,
+  S_DIAG, S_CONVERT, S_SETUP,
   S_NSITES
 };
 extern const char* const kSiteNames[S_NSITES];

@@ -125,7 +125,7 @@ template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
                                       const TC* D, bool jac, double rtol2, int max_iter) {
   const int nb = pw_blocks(c);
-  LaunchScope ls(c, S_CG_UPDATE);
+  LaunchScope ls(c, sizeof(TC) == 4 ? S_CG_UPDATE32 : S_CG_UPDATE64);
   if (jac)
     k_cg_update<TC, true><<<nb, kThreads, 0, c->stream>>>(x, r, p, Hp, D, (TC)c->jac_c, c->n3(),
                                                            red_args(c), rtol2, max_iter);
@@ -139,7 +139,7 @@ template <typename T, typename TC>
 void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,
                    bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2) {
-  LaunchScope ls(c, S_NEWTON_UPDATE);
+  LaunchScope ls(c, sizeof(T) == 4 ? S_NEWTON_UPDATE32 : S_NEWTON_UPDATE64);
   k_newton_update<T, TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(
       s, y, g, r, xi, D, N, w, nbar, c->mu, tau, c->jac_c, jac ? 1 : 0, s2, y2, g2, D2, r2,
       c->n3(), red_args(c));

@@ -4,7 +4,8 @@
 //
 // One Newton step:
 //   1. CG on H xi = -g (r = -g and r^T M^-1 r come from the gradient), to a
-//      relative residual eta = min(eta_max, sqrt(||g|| / ||g0||));
+//      relative residual eta = min(eta_max, max(sqrt(rel), 0.3 tol / rel)),
+//      rel = ||g|| / ||g0||;
 //   2. tau from Eq. (New5), tau = -xi^T g / xi^T H xi, with both sums taken
 //      from the CG recurrences (xi^T b = sum alpha_k r_k^T z_k,
 //      xi^T H xi = sum alpha_k^2 p_k^T H p_k), capped so max |tau xi| <=
@@ -19,8 +20,9 @@
 // rounding of each carried increment is relative to the gradient at that
 // step, so after that FP64 refresh the gradient stays accurate to FP64
 // relative to ||g0|| (iterative refinement).  PLC_MIXED keeps s, y, g in FP32
-// while ||g|| / ||g0|| >= mixed_switch, in FP64 after that; the stopping test
-// is only passed in FP64.  The CG runs in the precision of its fields (FP32
+// while ||g|| / ||g0|| >= max(mixed_switch, tol) and the FP32 steps still
+// converge, in FP64 after that; the stopping test is only passed on an FP64
+// gradient, so a solve that reaches tol in FP32 ends with one FP64 refresh.  The CG runs in the precision of its fields (FP32
 // for PLC_MIXED).
 #include <algorithm>
 #include <chrono>
@@ -152,20 +154,28 @@ plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar
   S.g0_norm = g0;
   plc_status status = PLC_OK;
   int it = 0, prev_cg = 1;
+  double prev_rel = 1.0;
   for (;;) {
     const double gnorm = std::sqrt(gs.gg);
     if (!std::isfinite(gnorm) || !std::isfinite(gs.f())) { status = PLC_ERR_NONFINITE; break; }
     const double rel = g0 > 0.0 ? gnorm / g0 : 0.0;
     S.grad_rel = rel;
     S.neg_logpost = gs.f();
-    if (!fp64 && (rel < o.mixed_switch || rel < o.tol)) {
+    // FP32 -> FP64: below the switch point, at the tolerance, or when an
+    // FP32 Newton step in the fast-convergence range (rel < 1e-3) fails to
+    // halve the gradient (the FP32 rounding floor)
+    if (!fp64 && (rel < o.mixed_switch || rel < o.tol ||
+                  (it > 0 && rel < 1e-3 && rel > 0.5 * prev_rel))) {
       gs = to_fp64();
       continue;
     }
+    prev_rel = rel;
     if (rel < o.tol) break;
     if (it >= o.max_newton) { status = PLC_ERR_NOT_CONVERGED; break; }
     // 1. inexact Newton direction
-    const double eta = std::min(o.eta_max, std::sqrt(rel));
+    // forcing term: superlinear sqrt(rel), but no tighter than the stop test
+    // needs (0.3 tol / rel) and never above eta_max
+    const double eta = std::min(o.eta_max, std::max(std::sqrt(rel), 0.3 * o.tol / rel));
     const int iters = run_cg<TC>(c, x, as<TC>(cur.r), p, Hp, as<TC>(cur.D), jac, eta * eta,
                                  o.max_cg, o.cg_chunk, prev_cg);
     prev_cg = iters;
