@@ -6,6 +6,7 @@
 #include "ctx.h"
 #include "ops.cuh"
 #include "passes.cuh"
+#include "passes4.cuh"
 
 namespace plc {
 
@@ -26,6 +27,39 @@ template <typename T, auto Kernel> inline void set_smem() {
 
 inline RedArgs red_args(plc_ctx* c) { return RedArgs{c->partials, c->sc}; }
 
+// The FP32 passes with register four-step line transforms (passes4.cuh).
+template <int N1, int N2, typename Pro, typename Epi, typename Fin>
+void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0) {
+  using Gm = Geo4<N1, N2>;
+  constexpr int n = Gm::N, h = n / 2 + 1;
+  float2* A = static_cast<float2*>(c->specA);
+  float2* B = static_cast<float2*>(c->specB);
+  const float2* tw = c->tw32;
+  const dim3 gx(n / Gm::RY, n), gy(n / Gm::L, h);
+  {
+    LaunchScope ls(c, Site(s0 + 0));
+    k4_xf<N1, N2, Pro><<<gx, kThreads, Gm::smem_x, c->stream>>>(pro, A, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 1));
+    k4_yf<N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(A, B, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 2));
+    k4_z<N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(B, c->M32, zero_dc, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 3));
+    k4_yi<N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(B, A, tw, done);
+  }
+  {
+    LaunchScope ls(c, Site(s0 + 4));
+    k4_xi<N1, N2, Epi, Fin><<<gx, kThreads, Gm::smem_x, c->stream>>>(A, epi, fin, red_args(c),
+                                                                     tw, done);
+  }
+  check(cudaGetLastError(), "spectral pipeline launch");
+}
+
 // The five passes XF -> YF -> Z -> YI -> XI on the context's stream.
 template <typename T, typename Pro, typename Epi, typename Fin>
 void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done,
@@ -33,6 +67,17 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
   using G = PassGeom<T>;
   const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
                                 : (sizeof(T) == 8 ? S_XF64 : S_XF32);
+  if constexpr (sizeof(T) == 4) {
+    switch (c->plan.f1 * 64 + c->plan.f2) {
+      case 16 * 64 + 16: return run_pipeline4<16, 16>(c, pro, epi, fin, zero_dc, done, s0);
+      case 16 * 64 + 12: return run_pipeline4<16, 12>(c, pro, epi, fin, zero_dc, done, s0);
+      case 16 * 64 + 8: return run_pipeline4<16, 8>(c, pro, epi, fin, zero_dc, done, s0);
+      case 12 * 64 + 8: return run_pipeline4<12, 8>(c, pro, epi, fin, zero_dc, done, s0);
+      case 8 * 64 + 8: return run_pipeline4<8, 8>(c, pro, epi, fin, zero_dc, done, s0);
+      case 8 * 64 + 4: return run_pipeline4<8, 4>(c, pro, epi, fin, zero_dc, done, s0);
+      default: break;
+    }
+  }
   const int n = c->n, h = n / 2 + 1;
   const size_t sm = G::smem_bytes(c->plan);
   cpx<T>* A = static_cast<cpx<T>*>(c->specA);

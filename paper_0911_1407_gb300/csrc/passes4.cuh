@@ -1,0 +1,399 @@
+// passes4.cuh -- the five FP32 passes of S^-1 (Sec. 2.2) with the line
+// transforms done four-step straight out of and into registers.
+//
+// Same pipeline and global layouts as passes.cuh (XF -> A[z][kx][y] -> YF ->
+// B[kx][ky][z] -> Z -> YI -> A -> XI), for n = N1 N2 with (N1, N2) in
+// {(16,16), (16,12), (16,8), (12,8), (8,8), (8,4)}.  A line of length N is
+// transformed in two register phases joined by one shared-memory exchange:
+//
+//   forward  Z[k1 + N1 k2] = sum_n2 W_N2^{n2 k2} W_N^{n2 k1}
+//                                   sum_n1 W_N1^{n1 k1} x[N2 n1 + n2]
+//     phase A, task (line c, n2): DFT_N1 of x[N2 n1 + n2] over n1, twiddle
+//     phase B, task (line c, k1): DFT_N2 over n2 -> Z[k1 + N1 k2]
+//   inverse  x[N2 n1 + n2] = sum_k1 W_N1^{-n1 k1} W_N^{-n2 k1}
+//                                   sum_k2 W_N2^{-n2 k2} Z[k1 + N1 k2]
+//     phase B' (c, k1): inverse DFT_N2 over k2, conjugate twiddle
+//     phase A' (c, n2): inverse DFT_N1 over k1 -> x[N2 n1 + n2]
+//
+// Each phase reads or writes global memory directly from the registers of
+// its task, choosing the lane order that makes the access coalesced: a
+// phase that walks a line along its own (contiguous) axis puts n2 (or its
+// position) on consecutive lanes; a phase that writes the line index as the
+// contiguous axis (B[kx][ky][z] seen from the y pass) puts the line c on
+// consecutive lanes.  The exchange buffer X[c][k1 N2 + n2] has an odd pitch
+// N + 1 so that both lane orders are free of bank conflicts, and the
+// twiddles sit in shared memory as tw2[k1 N2 + n2] = W_N^{k1 n2}.
+//
+// The x passes pack two real rows as one complex line.  Their phase B (XF)
+// and B' (XI) run as pairs of tasks k1 and N1 - k1 on the two half-warps of
+// one warp, which hold the partner frequencies N - k of each other's k, so
+// the real-to-complex split and its inverse take a warp shuffle instead of
+// another trip through shared memory.  The prologue and epilogue see rows in
+// natural order through a staging buffer of real rows (pitch N + 8 floats),
+// so they keep their 16-byte vector accesses.
+#pragma once
+
+#include "passes.cuh"
+
+namespace plc {
+
+template <int N1_, int N2_> struct Geo4 {
+  static constexpr int N1 = N1_, N2 = N2_, N = N1 * N2;
+  static constexpr int L = 16;            // lines per block
+  static constexpr int S = N + 1;         // pitch of the exchange buffer (float2)
+  static constexpr int RY = 2 * L;        // real rows per x-pass block
+  static constexpr int SR = N + 8;        // pitch of the real-row staging (floats)
+  static constexpr size_t tw_bytes = sizeof(float2) * N;
+  static constexpr size_t x_bytes = sizeof(float2) * L * S;
+  static constexpr size_t r_bytes = sizeof(float) * RY * SR;
+  static constexpr size_t smem_y = tw_bytes + x_bytes;
+  static constexpr size_t smem_x = tw_bytes + (x_bytes > r_bytes ? x_bytes : r_bytes);
+  static_assert(L * N2 <= kThreads, "one phase-A task per thread at most");
+  static_assert(N1 / 2 <= kThreads / 32, "one warp per pair of x-pass tasks");
+};
+
+// tw2[k1 N2 + n2] = W_N^{k1 n2} from the natural table tw[m] = W_N^m.
+template <int N1, int N2>
+__device__ __forceinline__ void load_tw2(float2* tw2, const float2* __restrict__ twg) {
+  for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) tw2[i] = twg[(i / N2) * (i % N2)];
+}
+
+// Phase A: DFT_N1 over n1 (sign SIGN), then twiddle by W_N^{SIGN-conjugated n2 k1}.
+template <int N1, int N2, int SIGN>
+__device__ __forceinline__ void phase_a(float2* v, const float2* tw2, int n2) {
+  dft_small<float, SIGN, N1>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) {
+    float2 w = tw2[k1 * N2 + n2];
+    if (SIGN > 0) w.y = -w.y;
+    v[k1] = cmul(v[k1], w);
+  }
+}
+
+// Phase B': inverse DFT_N2 over k2, then the conjugate twiddle W_N^{-n2 k1}.
+template <int N1, int N2>
+__device__ __forceinline__ void phase_b_inv(float2* v, const float2* tw2, int k1) {
+  dft_small<float, +1, N2>(v);
+#pragma unroll
+  for (int n2 = 1; n2 < N2; ++n2) {
+    float2 w = tw2[k1 * N2 + n2];
+    w.y = -w.y;
+    v[n2] = cmul(v[n2], w);
+  }
+}
+
+#define PLC_PASS4_PROLOGUE(SMEM_TAIL)                                   \
+  using Gm = Geo4<N1, N2>;                                              \
+  constexpr int N = Gm::N;                                              \
+  if (done && *done) return;                                            \
+  extern __shared__ __align__(16) unsigned char smem_raw[];             \
+  float2* tw2 = reinterpret_cast<float2*>(smem_raw);                    \
+  SMEM_TAIL;                                                            \
+  load_tw2<N1, N2>(tw2, twg);                                           \
+  __syncthreads()
+
+// ---------------------------------------------------------------------------
+// YF: c2c along y.  grid = (n / 16, n/2+1); block (zb, kx) owns the lines
+// A[z0 + c][kx][:] and writes B[kx][:][z0 + c].
+// ---------------------------------------------------------------------------
+template <int N1, int N2>
+__global__ void __launch_bounds__(kThreads)
+k4_yf(const float2* __restrict__ A, float2* __restrict__ B, const float2* __restrict__ twg,
+      const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(float2* X = tw2 + N);
+  const int h = N / 2 + 1, z0 = blockIdx.x * Gm::L, kx = blockIdx.y;
+  if (threadIdx.x < Gm::L * N2) {
+    const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
+    const float2* src = A + ((size_t)(z0 + c) * h + kx) * N + n2;
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[N2 * n1];
+    phase_a<N1, N2, -1>(v, tw2, n2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) X[c * Gm::S + k1 * N2 + n2] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
+    const int c = t % Gm::L, k1 = t / Gm::L;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = X[c * Gm::S + k1 * N2 + n2];
+    dft_small<float, -1, N2>(v);
+    float2* dst = B + ((size_t)kx * N + k1) * N + z0 + c;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) dst[(size_t)N1 * k2 * N] = v[k2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Z: forward c2c along z, times M[|m|^2] = 1/(lambda_k n^3), inverse c2c,
+// in place.  grid = (n / 16, n/2+1); block (kyb, kx) owns B[kx][ky0 + c][:].
+// The spectrum of each phase-B task stays in registers between the two
+// transforms.  zero_dc drops the DC mode.
+// ---------------------------------------------------------------------------
+template <int N1, int N2>
+__global__ void __launch_bounds__(kThreads)
+k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
+     const float2* __restrict__ twg, const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(float2* X = tw2 + N);
+  const int ky0 = blockIdx.x * Gm::L, kx = blockIdx.y;
+  float2* line0 = B + ((size_t)kx * N + ky0) * N;
+  const bool task_a = threadIdx.x < Gm::L * N2;
+  const int n2a = threadIdx.x % N2, ca = threadIdx.x / N2;
+  float2 v[N1 > N2 ? N1 : N2];
+  if (task_a) {
+    const float2* src = line0 + (size_t)ca * N + n2a;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[N2 * n1];
+    phase_a<N1, N2, -1>(v, tw2, n2a);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) X[ca * Gm::S + k1 * N2 + n2a] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
+    const int c = t % Gm::L, k1 = t / Gm::L;
+    float2 u[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) u[n2] = X[c * Gm::S + k1 * N2 + n2];
+    dft_small<float, -1, N2>(u);
+    const int ky = ky0 + c, my = min(ky, N - ky);
+    const int mxy = kx * kx + my * my;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int kz = k1 + N1 * k2, mz = min(kz, N - kz);
+      const int m2 = mxy + mz * mz;
+      const float f = (zero_dc && m2 == 0) ? 0.f : __ldg(M + m2);
+      u[k2] = cscale(u[k2], f);
+    }
+    phase_b_inv<N1, N2>(u, tw2, k1);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = u[n2];
+  }
+  __syncthreads();
+  if (task_a) {
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = X[ca * Gm::S + k1 * N2 + n2a];
+    dft_small<float, +1, N1>(v);
+    float2* dst = line0 + (size_t)ca * N + n2a;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) dst[N2 * n1] = v[n1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// YI: inverse c2c along y.  grid = (n / 16, n/2+1); block (zb, kx) reads
+// B[kx][:][z0 + c] and writes A[z0 + c][kx][:].
+// ---------------------------------------------------------------------------
+template <int N1, int N2>
+__global__ void __launch_bounds__(kThreads)
+k4_yi(const float2* __restrict__ B, float2* __restrict__ A, const float2* __restrict__ twg,
+      const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(float2* X = tw2 + N);
+  const int h = N / 2 + 1, z0 = blockIdx.x * Gm::L, kx = blockIdx.y;
+  for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
+    const int c = t % Gm::L, k1 = t / Gm::L;
+    const float2* src = B + ((size_t)kx * N + k1) * N + z0 + c;
+    float2 u[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) u[k2] = src[(size_t)N1 * k2 * N];
+    phase_b_inv<N1, N2>(u, tw2, k1);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = u[n2];
+  }
+  __syncthreads();
+  if (threadIdx.x < Gm::L * N2) {
+    const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
+    float2 v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = X[c * Gm::S + k1 * N2 + n2];
+    dft_small<float, +1, N1>(v);
+    float2* dst = A + ((size_t)(z0 + c) * h + kx) * N + n2;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) dst[N2 * n1] = v[n1];
+  }
+}
+
+// Frequencies of the paired x-pass tasks: warp g < N1/2 takes k1 = g and
+// N1 - g on its two half-warps (g = 0: k1 = 0 and N1/2, each its own partner).
+template <int N1> __device__ __forceinline__ int pair_k1(int g, int member) {
+  return g == 0 ? (member ? N1 / 2 : 0) : (member ? N1 - g : g);
+}
+
+__device__ __forceinline__ float2 shfl_xor16(float2 a) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, 16), __shfl_xor_sync(0xffffffffu, a.y, 16));
+}
+
+// ---------------------------------------------------------------------------
+// XF: r2c along x + prologue.  grid = (n / 32, n); block (yb, z) owns rows
+// y0 .. y0+31 of plane z; rows 2c and 2c+1 form complex line c.  With
+// Z = FFT(row_2c + i row_2c+1): X_a[k] = (Z[k] + conj Z[N-k]) / 2 and
+// X_b[k] = (Z[k] - conj Z[N-k]) / 2i, stored as a pair at A[z][k][y0+2c].
+// ---------------------------------------------------------------------------
+template <int N1, int N2, typename Pro>
+__global__ void __launch_bounds__(kThreads)
+k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
+      const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(float* R = reinterpret_cast<float*>(tw2 + N); float2* X = tw2 + N);
+  pro.prepare();
+  const int h = N / 2 + 1, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
+  // prologue: 32 rows in natural order, four x per thread and step
+  constexpr int Q = N / 4, TOT = Gm::RY * Q, B4 = 4;
+  const size_t row0 = ((size_t)z * N + y0) * N;
+  for (int base = threadIdx.x; base < TOT; base += B4 * kThreads) {
+    V4<float> u[B4];
+#pragma unroll
+    for (int q = 0; q < B4; ++q) {
+      const int e = base + q * kThreads;
+      if (e < TOT) u[q] = pro.vec4(row0 + (size_t)(e / Q) * N + 4 * (e % Q));
+    }
+#pragma unroll
+    for (int q = 0; q < B4; ++q) {
+      const int e = base + q * kThreads;
+      if (e < TOT)
+        *reinterpret_cast<float4*>(&R[(e / Q) * Gm::SR + 4 * (e % Q)]) =
+            make_float4(u[q].v[0], u[q].v[1], u[q].v[2], u[q].v[3]);
+    }
+  }
+  __syncthreads();
+  // phase A on (c, n2), n2 on consecutive lanes
+  const bool task_a = threadIdx.x < Gm::L * N2;
+  const int n2a = threadIdx.x % N2, ca = threadIdx.x / N2;
+  float2 v[N1 > N2 ? N1 : N2];
+  if (task_a) {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1)
+      v[n1] = make_float2(R[(2 * ca) * Gm::SR + N2 * n1 + n2a],
+                          R[(2 * ca + 1) * Gm::SR + N2 * n1 + n2a]);
+    phase_a<N1, N2, -1>(v, tw2, n2a);
+  }
+  __syncthreads();   // X overlays R
+  if (task_a) {
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) X[ca * Gm::S + k1 * N2 + n2a] = v[k1];
+  }
+  __syncthreads();
+  // phase B in pairs k1, N1 - k1 (one warp per pair), split into X_a, X_b
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (g < N1 / 2) {
+    const int c = lane & 15, member = lane >> 4;
+    const int k1 = pair_k1<N1>(g, member);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = X[c * Gm::S + k1 * N2 + n2];
+    dft_small<float, -1, N2>(v);
+    float2* dst = A + ((size_t)z * h + k1) * N + y0 + 2 * c;
+    auto put = [&](int k2, float2 zk, float2 zm) {   // zm = Z[N - k]
+      const float2 zc = cconj(zm);
+      const float2 s = cadd(zk, zc), d = csub(zk, zc);
+      st_pair(dst + (size_t)N1 * k2 * N, make_float2(0.5f * s.x, 0.5f * s.y),
+              make_float2(0.5f * d.y, -0.5f * d.x));
+    };
+    if (g != 0) {
+      // Z[N - (k1 + N1 k2)] is the partner's element N2 - 1 - k2
+      float2 pz[N2 / 2];
+#pragma unroll
+      for (int j = 0; j < N2 / 2; ++j) pz[j] = shfl_xor16(v[N2 - 1 - j]);
+#pragma unroll
+      for (int k2 = 0; k2 < N2 / 2; ++k2) put(k2, v[k2], pz[k2]);
+    } else if (member == 0) {
+      // k = N1 k2, N - k = N1 (N2 - k2): own elements, k2 = 0 .. N2/2
+#pragma unroll
+      for (int k2 = 0; k2 <= N2 / 2; ++k2) put(k2, v[k2], v[(N2 - k2) % N2]);
+    } else {
+      // k = N1/2 + N1 k2, N - k = N1/2 + N1 (N2 - 1 - k2)
+#pragma unroll
+      for (int k2 = 0; k2 < N2 / 2; ++k2) put(k2, v[k2], v[N2 - 1 - k2]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// XI: c2r along x + epilogue.  grid = (n / 32, n).  Line c is rebuilt from
+// Z[k] = X_a[k] + i X_b[k] and Z[N-k] = conj X_a[k] + i conj X_b[k] (k <= n/2);
+// the imaginary parts of the k = 0 and k = n/2 coefficients are dropped
+// (projection onto real fields).  The epilogue sees y = (S^-1 x)_i per cell
+// and accumulates Epi::NV sums; Fin runs once on the grid totals.
+// ---------------------------------------------------------------------------
+template <int N1, int N2, typename Epi, typename Fin>
+__global__ void __launch_bounds__(kThreads)
+k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
+      const float2* __restrict__ twg, const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(float* R = reinterpret_cast<float*>(tw2 + N); float2* X = tw2 + N);
+  const int h = N / 2 + 1, nh = N / 2, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
+  const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2 v[N1 > N2 ? N1 : N2];
+  if (g < N1 / 2) {
+    const int c = lane & 15, member = lane >> 4;
+    const int k1 = pair_k1<N1>(g, member);
+    const float2* src = A + ((size_t)z * h + k1) * N + y0 + 2 * c;
+    // own coefficients k = k1 + N1 k2 <= n/2: Z[k] and the partner form Zc
+    constexpr int NL = N2 / 2 + 1;
+    float2 za[NL], zb[NL];
+    const int nload = (g == 0 && member == 0) ? N2 / 2 + 1 : N2 / 2;
+#pragma unroll
+    for (int k2 = 0; k2 < NL; ++k2)
+      if (k2 < nload) ld_pair(src + (size_t)N1 * k2 * N, za[k2], zb[k2]);
+    float2 zc[NL];
+#pragma unroll
+    for (int k2 = 0; k2 < NL; ++k2) {
+      if (k2 >= nload) continue;
+      float2 xa = za[k2], xb = zb[k2];
+      const int k = k1 + N1 * k2;
+      if (k == 0 || k == nh) { xa.y = 0.f; xb.y = 0.f; }
+      v[k2] = make_float2(xa.x - xb.y, xa.y + xb.x);
+      zc[k2] = make_float2(xa.x + xb.y, xb.x - xa.y);
+    }
+    if (g != 0) {
+      // Z[k1 + N1 k2] for k2 >= N2/2 is the partner's Zc at N2 - 1 - k2
+#pragma unroll
+      for (int j = 0; j < N2 / 2; ++j) v[N2 - 1 - j] = shfl_xor16(zc[j]);
+    } else if (member == 0) {
+#pragma unroll
+      for (int k2 = N2 / 2 + 1; k2 < N2; ++k2) v[k2] = zc[N2 - k2];
+    } else {
+#pragma unroll
+      for (int k2 = N2 / 2; k2 < N2; ++k2) v[k2] = zc[N2 - 1 - k2];
+    }
+    phase_b_inv<N1, N2>(v, tw2, k1);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = v[n2];
+  }
+  __syncthreads();
+  const bool task_a = threadIdx.x < Gm::L * N2;
+  const int n2a = threadIdx.x % N2, ca = threadIdx.x / N2;
+  if (task_a) {
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = X[ca * Gm::S + k1 * N2 + n2a];
+    dft_small<float, +1, N1>(v);
+  }
+  __syncthreads();   // R overlays X
+  if (task_a) {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+      R[(2 * ca) * Gm::SR + N2 * n1 + n2a] = v[n1].x;
+      R[(2 * ca + 1) * Gm::SR + N2 * n1 + n2a] = v[n1].y;
+    }
+  }
+  __syncthreads();
+  typename Epi::Acc acc[Epi::NV > 0 ? Epi::NV : 1];
+#pragma unroll
+  for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
+  constexpr int Q = N / 4, TOT = Gm::RY * Q;
+  const size_t row0 = ((size_t)z * N + y0) * N;
+#pragma unroll 2
+  for (int e = threadIdx.x; e < TOT; e += kThreads) {
+    const int row = e / Q, x = 4 * (e % Q);
+    const float4 q = *reinterpret_cast<const float4*>(&R[row * Gm::SR + x]);
+    const V4<float> y{{q.x, q.y, q.z, q.w}};
+    epi.vec4(row0 + (size_t)row * N + x, y, acc);
+  }
+  if constexpr (Epi::NV > 0) {
+    double tot[Epi::NV];
+#pragma unroll
+    for (int j = 0; j < Epi::NV; ++j) tot[j] = acc[j].get();
+    block_reduce_finish<Epi::NV, Epi::MAXMASK>(tot, ra, fin);
+  }
+}
+
+#undef PLC_PASS4_PROLOGUE
+
+}  // namespace plc
