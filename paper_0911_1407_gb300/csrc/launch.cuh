@@ -46,7 +46,7 @@ void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int
   }
   {
     LaunchScope ls(c, Site(s0 + 2));
-    k4_z<N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(B, c->M32, zero_dc, tw, done);
+    k4_z<N1, N2><<<gy, kThreads, Gm::smem_z, c->stream>>>(B, c->M32, zero_dc, tw, done);
   }
   {
     LaunchScope ls(c, Site(s0 + 3));

@@ -48,6 +48,7 @@ __device__ __forceinline__ double jacobi(double r, double d, double c) { return 
 template <typename T> struct ProLoad {
   const T* x;
   __device__ void prepare() {}
+  __device__ void prefetch(size_t i, unsigned cnt) const { prefetch_l2(x + i, cnt * sizeof(T)); }
   __device__ T operator()(size_t i) const { return __ldg(x + i); }
   __device__ V4<T> vec4(size_t i) const { return ld4(x + i); }
 };
@@ -58,6 +59,7 @@ template <typename T, typename TS> struct ProShift {
   const TS* s;
   double mu;
   __device__ void prepare() {}
+  __device__ void prefetch(size_t i, unsigned cnt) const { prefetch_l2(s + i, cnt * sizeof(TS)); }
   // difference taken in the transform precision (no FP64 work for float)
   __device__ T operator()(size_t i) const { return (T)__ldg(s + i) - (T)mu; }
   __device__ V4<T> vec4(size_t i) const {
@@ -79,6 +81,11 @@ template <typename T, bool JAC> struct ProCgDir {
   const DevScalars* sc;
   T beta;              // loaded by prepare()
   __device__ void prepare() { beta = (T)__ldg(&sc->beta); }
+  __device__ void prefetch(size_t i, unsigned cnt) const {
+    prefetch_l2(r + i, cnt * sizeof(T));
+    if (JAC) prefetch_l2(D + i, cnt * sizeof(T));
+    if (beta != (T)0) prefetch_l2(p + i, cnt * sizeof(T));
+  }
   __device__ T operator()(size_t i) const {
     const T ri = __ldg(r + i);
     const T zi = JAC ? jacobi(ri, __ldg(D + i), c) : ri;
@@ -107,6 +114,7 @@ template <typename T> struct EpiStore {
   static constexpr unsigned MAXMASK = 0;
   using Acc = AccD;
   T* out;
+  __device__ void prefetch(size_t, unsigned) const {}
   __device__ void operator()(size_t i, T y, Acc*) const { out[i] = y; }
   __device__ void vec4(size_t i, const V4<T>& y, Acc*) const { st4(out + i, y); }
 };
@@ -121,6 +129,11 @@ template <typename T> struct EpiHessS {
   const T* v;
   T* out;
   using Acc = AccD;
+  __device__ void prefetch(size_t i, unsigned cnt) const {
+    prefetch_l2(s + i, cnt * sizeof(T));
+    prefetch_l2(v + i, cnt * sizeof(T));
+    if (w) prefetch_l2(w + i, cnt * sizeof(T));
+  }
   __device__ void operator()(size_t i, T y, Acc*) const {
     const T d = nbar * (w ? __ldg(w + i) : (T)1) * exp(__ldg(s + i));
     out[i] = y + d * __ldg(v + i);
@@ -143,6 +156,10 @@ template <typename T> struct EpiHessD {
   const T* v;
   T* out;
   using Acc = typename AccOf<T>::type;
+  __device__ void prefetch(size_t i, unsigned cnt) const {
+    prefetch_l2(D + i, cnt * sizeof(T));
+    prefetch_l2(v + i, cnt * sizeof(T));
+  }
   __device__ void operator()(size_t i, T y, Acc* acc) const {
     const T vi = __ldg(v + i);
     const T hv = y + __ldg(D + i) * vi;
@@ -181,6 +198,11 @@ template <typename T, typename TS, typename TW, typename TC> struct EpiGrad {
   TC* r;                // may be null
   double c;             // Jacobi constant (S^-1)_ii
   int jac;
+  __device__ void prefetch(size_t i, unsigned cnt) const {
+    prefetch_l2(s + i, cnt * sizeof(TS));
+    prefetch_l2(N + i, cnt * sizeof(int32_t));
+    if (w) prefetch_l2(w + i, cnt * sizeof(TW));
+  }
   // one cell: returns g and d, accumulates the sums
   __device__ __forceinline__ void cell(T st, T wt, T ni, T y, Acc* acc, T& gi, T& d) const {
     d = (T)nbar * wt * exp(st);
@@ -230,6 +252,7 @@ template <typename T, typename TL> struct EpiDot {
   static constexpr unsigned MAXMASK = 0;
   const TL* lam;
   using Acc = AccD;
+  __device__ void prefetch(size_t i, unsigned cnt) const { prefetch_l2(lam + i, cnt * sizeof(TL)); }
   __device__ void operator()(size_t i, T y, Acc* acc) const {
     acc[0].add((double)__ldg(lam + i) * (double)y);
   }

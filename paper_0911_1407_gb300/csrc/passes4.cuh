@@ -46,7 +46,9 @@ template <int N1_, int N2_> struct Geo4 {
   static constexpr size_t tw_bytes = sizeof(float2) * N;
   static constexpr size_t x_bytes = sizeof(float2) * L * S;
   static constexpr size_t r_bytes = sizeof(float) * RY * SR;
+  static constexpr size_t m_bytes = sizeof(float) * L * (N / 2 + 1);   // Z multipliers
   static constexpr size_t smem_y = tw_bytes + x_bytes;
+  static constexpr size_t smem_z = tw_bytes + x_bytes + m_bytes;
   static constexpr size_t smem_x = tw_bytes + (x_bytes > r_bytes ? x_bytes : r_bytes);
   static_assert(L * N2 <= kThreads, "one phase-A task per thread at most");
   static_assert(N1 / 2 <= kThreads / 32, "one warp per pair of x-pass tasks");
@@ -135,7 +137,8 @@ template <int N1, int N2>
 __global__ void __launch_bounds__(kThreads)
 k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
      const float2* __restrict__ twg, const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(float2* X = tw2 + N);
+  PLC_PASS4_PROLOGUE(float2* X = tw2 + N;
+                     float* Ms = reinterpret_cast<float*>(X + Gm::L * Gm::S));
   const int ky0 = blockIdx.x * Gm::L, kx = blockIdx.y;
   float2* line0 = B + ((size_t)kx * N + ky0) * N;
   const bool task_a = threadIdx.x < Gm::L * N2;
@@ -145,6 +148,25 @@ k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
     const float2* src = line0 + (size_t)ca * N + n2a;
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[N2 * n1];
+  }
+  // while the lines load: the block's multipliers Ms[c][|mz|] =
+  // M[kx^2 + my^2 + mz^2], gathered from the L2-resident table
+  constexpr int HM = N / 2 + 1, MI = (Gm::L * HM + kThreads - 1) / kThreads;
+  float mv[MI];
+#pragma unroll
+  for (int j = 0; j < MI; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    const int c = i / HM, mz = i - c * HM;
+    const int ky = ky0 + c, my = min(ky, N - ky);
+    const int m2 = kx * kx + my * my + mz * mz;
+    mv[j] = (i >= Gm::L * HM || (zero_dc && m2 == 0)) ? 0.f : __ldg(M + m2);
+  }
+#pragma unroll
+  for (int j = 0; j < MI; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    if (i < Gm::L * HM) Ms[i] = mv[j];
+  }
+  if (task_a) {
     phase_a<N1, N2, -1>(v, tw2, n2a);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) X[ca * Gm::S + k1 * N2 + n2a] = v[k1];
@@ -156,14 +178,10 @@ k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) u[n2] = X[c * Gm::S + k1 * N2 + n2];
     dft_small<float, -1, N2>(u);
-    const int ky = ky0 + c, my = min(ky, N - ky);
-    const int mxy = kx * kx + my * my;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       const int kz = k1 + N1 * k2, mz = min(kz, N - kz);
-      const int m2 = mxy + mz * mz;
-      const float f = (zero_dc && m2 == 0) ? 0.f : __ldg(M + m2);
-      u[k2] = cscale(u[k2], f);
+      u[k2] = cscale(u[k2], Ms[c * HM + mz]);
     }
     phase_b_inv<N1, N2>(u, tw2, k1);
 #pragma unroll
@@ -236,9 +254,11 @@ k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
   PLC_PASS4_PROLOGUE(float* R = reinterpret_cast<float*>(tw2 + N); float2* X = tw2 + N);
   pro.prepare();
   const int h = N / 2 + 1, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
-  // prologue: 32 rows in natural order, four x per thread and step
+  // prologue: 32 rows in natural order, four x per thread and step; the
+  // block's rows are contiguous and are first requested into L2 whole
   constexpr int Q = N / 4, TOT = Gm::RY * Q, B4 = 4;
   const size_t row0 = ((size_t)z * N + y0) * N;
+  if (threadIdx.x == 0) pro.prefetch(row0, Gm::RY * N);
   for (int base = threadIdx.x; base < TOT; base += B4 * kThreads) {
     V4<float> u[B4];
 #pragma unroll
@@ -319,6 +339,10 @@ k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
       const float2* __restrict__ twg, const int* __restrict__ done) {
   PLC_PASS4_PROLOGUE(float* R = reinterpret_cast<float*>(tw2 + N); float2* X = tw2 + N);
   const int h = N / 2 + 1, nh = N / 2, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
+  const size_t row0 = ((size_t)z * N + y0) * N;
+  // the epilogue's operands do not depend on the transform: request them
+  // into L2 now, so that their latency hides behind the transform
+  if (threadIdx.x == 0) epi.prefetch(row0, Gm::RY * N);
   const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2 v[N1 > N2 ? N1 : N2];
   if (g < N1 / 2) {
@@ -378,7 +402,6 @@ k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
 #pragma unroll
   for (int j = 0; j < Epi::NV; ++j) acc[j].init((Epi::MAXMASK >> j) & 1u);
   constexpr int Q = N / 4, TOT = Gm::RY * Q;
-  const size_t row0 = ((size_t)z * N + y0) * N;
 #pragma unroll 2
   for (int e = threadIdx.x; e < TOT; e += kThreads) {
     const int row = e / Q, x = 4 * (e % Q);

@@ -117,3 +117,32 @@ def test_vjp_matches_oracle(plc, precision, bar):
     vN, vA, st = c.map_vjp(dev(ref.s, torch.float64), None, m.nbar, dev(u, torch.float64), tol=tol)
     assert rel_l2(host(vN), lam_ref) <= bar
     assert abs(vA - lnA_ref) <= bar * abs(lnA_ref)
+
+
+@pytest.mark.parametrize("key,precision", [("selection128", "fp64"), ("selection128", "mixed"),
+                                           ("production256", "mixed")])
+def test_map_full_size_is_a_map_for_the_oracle(plc, key, precision):
+    """At the full workload sizes the GPU MAP (stopped at ||g|| / ||g0|| < 1e-6)
+    must be a MAP by the oracle's own gradient: one FP64 oracle gradient at
+    s_gpu gives the same relative norm, below the tolerance, and the flat-mean
+    invariant sum w nbar e^s = sum N holds."""
+    m = mocks.make_mock(mocks.WORKLOADS[key])
+    s, st = _gpu_map(plc, m, precision, 1e-6)
+    assert st["grad_rel"] < 1e-6
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab)
+    g0 = np.linalg.norm(orc.gradient(np.full(m.N.shape, m.mu), p))
+    rel = np.linalg.norm(orc.gradient(s, p)) / g0
+    assert rel < 1e-6
+    assert abs(rel - st["grad_rel"]) <= 1e-3 * st["grad_rel"]
+    D = p.wn * np.exp(s)
+    assert abs(D.sum() - m.N.sum()) <= 1e-4 * m.N.sum()
+
+
+def test_map_mixed_vs_fp64_selection128(plc):
+    """128^3 with radial selection and angular mask: the mixed-precision MAP
+    against the FP64 GPU MAP, both stopped at ||g|| / ||g0|| < 1e-6."""
+    m = mocks.make_mock(mocks.WORKLOADS["selection128"])
+    s64, _ = _gpu_map(plc, m, "fp64", 1e-6)
+    s32, _ = _gpu_map(plc, m, "mixed", 1e-6)
+    assert np.max(np.abs(s32 - s64)) <= 1e-4
+    assert rel_l2(s32, s64) <= 1e-5
