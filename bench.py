@@ -294,7 +294,8 @@ def main(argv=None):
         dist.barrier()
     clk = clocks.stop()
     t_dev = e0.elapsed_time(e1) / 1e3
-    launches = int(sum(v[0] for v in ctx.profile_read().values()))
+    # each solve is one graph launch; the library counts the kernels it ran
+    launches = int(sum(st["kernels"] for st in stats))
     if world > 1:
         t = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -304,13 +305,16 @@ def main(argv=None):
     # ---------------- second timed region with per-launch CUDA events --------
     # (the events add a little host and device time, so `value` above is
     # taken without them; the kernel durations and the roofline come from here)
-    # CG chunks of one iteration here, so that no launch is an early exit
+    # The per-launch events need the host-driven form of the same solve (a
+    # graph cannot hold event records in its loops); it takes the same steps
+    # and launches the same kernels.  CG chunks of one iteration, so that no
+    # launch is an early exit.
     ctx.profile_enable(True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         s.fill_(m.mu)
-        ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, cg_chunk=1)
+        ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, cg_chunk=1, device_driven=0)
     e1.record(stream)
     torch.cuda.synchronize()
     t_prof = e0.elapsed_time(e1) / 1e3
@@ -506,6 +510,16 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
                             "cg": rs.stats["cg_iters"], "grad_rel": rs.stats["grad_rel"],
                             "max_abs_vs_fp64": float(dd.abs().max())}
     line["mixed_switch_sweep"] = sweep
+    # host-driven form of the same solve (host reads scalars per CG chunk)
+    for rep in range(2):
+        sm.fill_(m.mu)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.newton_krylov_map(N_dev, None, m.nbar, s=sm, tol=TOL, device_driven=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    line["host_driven_ms"] = e0.elapsed_time(e1)
+    batch_extra(plc, line)
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:
         t_hv, t_g = time_oracle_sample(m)
@@ -516,6 +530,63 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
             "sample": (f"one oracle Hv ({t_hv:.2f} s) and one gradient+objective ({t_g:.2f} s) at "
                        f"256^3, scaled by the FP64 solve's {hvc} Hv and {gc} gradients per MAP"),
             "hv_per_s": 1.0 / t_hv}
+
+
+def batch_extra(plc, line):
+    """64 independent mocks of uneven sizes (16 x 64^3, 32 x 96^3, 16 x 128^3,
+    sigma_G ~ U[0.8, 1.8], nbar log-uniform in [0.2, 2]), mixed precision, to
+    ||g|| / ||g0|| < 1e-6: one graph launch for all against one device-driven
+    solve after another on one stream."""
+    import torch
+    from paper_0911_1407_gb300 import mocks
+    ms = [mocks.make_mock(sp) for sp in mocks.batch_specs()]
+    cs = []
+    for m in ms:
+        c = plc.Context(m.n, m.box, "mixed")
+        c.set_prior(m.k_tab, m.P_tab, m.mu)
+        cs.append(c)
+    Ns = [torch.from_numpy(m.N).cuda() for m in ms]
+    ss = [torch.empty((m.n,) * 3, dtype=torch.float64, device="cuda") for m in ms]
+    nb = [m.nbar for m in ms]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one_by_one():
+        for c, m, N, s in zip(cs, ms, Ns, ss):
+            s.fill_(m.mu)
+            c.newton_krylov_map(N, None, m.nbar, s=s, tol=TOL)
+
+    b = plc.Batch(cs)
+
+    def batched():
+        for m, s in zip(ms, ss):
+            s.fill_(m.mu)
+        return b.map(Ns, None, nb, ss, tol=TOL)
+
+    times = {}
+    for name, fn in (("one_by_one", one_by_one), ("batched", batched)):
+        fn()                      # captures the graphs
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        times[name] = best
+    _, stats = out
+    line["batch"] = {
+        "mocks": len(ms), "sizes": "16x64^3, 32x96^3, 16x128^3", "precision": "mixed", "tol": TOL,
+        "maps_per_s_batched": len(ms) / times["batched"],
+        "maps_per_s_one_by_one": len(ms) / times["one_by_one"],
+        "speedup": times["one_by_one"] / times["batched"],
+        "newton_iters": sum(st["newton_iters"] for st in stats),
+        "cg_iters": sum(st["cg_iters"] for st in stats),
+        "kernels": sum(st["kernels"] for st in stats),
+        "max_grad_rel": max(st["grad_rel"] for st in stats)}
+    del b, cs
 
 
 if __name__ == "__main__":

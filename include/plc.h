@@ -113,6 +113,13 @@ typedef struct {
                           >= 1 means FP64 throughout).  The switch also happens when
                           an FP32 Newton step below 1e-3 fails to halve ||g||.  The
                           stopping test is always taken on an FP64 gradient. */
+  int device_driven;   /* 1: the solve's decisions are taken on the device and the
+                          whole solve is one CUDA graph launch (conditional nodes;
+                          captured on the first call and reused while N, w, nbar,
+                          s_inout, the prior and the options stay the same); 0: a
+                          host loop reads the device scalars after each gradient,
+                          CG chunk and trial.  Same iteration either way
+                          (default 1). */
 } plc_opts;
 
 typedef struct {
@@ -127,6 +134,7 @@ typedef struct {
   double g0_norm;      /* ||g0|| used */
   double neg_logpost;  /* final -ln P(s|N) (constants dropped) */
   double ms;           /* wall time of the call, milliseconds */
+  long long kernels;   /* kernels launched by the solve (device-driven solves) */
 } plc_stats;
 
 /* Fill *opts with the defaults above. */
@@ -157,6 +165,31 @@ plc_status plc_newton_krylov_map(plc_ctx* ctx, const int32_t* N, const void* w,
 plc_status plc_map_vjp(plc_ctx* ctx, const double* s_map, const void* w,
                        double nbar, const double* u, double* vjp_N,
                        double* vjp_lnA, const plc_opts* opts, plc_stats* stats);
+
+/* A batch of independent MAP solves (many mocks, each with its own grid
+ * size, prior, counts and selection; the paper has no counterpart): every
+ * context's device-driven solve is captured as its own chain of one CUDA
+ * graph, so the whole batch is one graph launch whose chains run
+ * concurrently.  plc_batch_create takes `count` contexts (each with its
+ * prior set; the batch does not own them, and they must outlive it and not
+ * be used concurrently with it). */
+typedef struct plc_batch plc_batch;
+
+plc_status plc_batch_create(plc_batch** batch, plc_ctx* const* ctxs, int count);
+
+/* Solve all: N[i] (int32), w[i] (double or NULL; w itself may be NULL for
+ * w = 1 everywhere), nbar[i] (host), s_inout[i] (double: start point in,
+ * MAP out) are context i's fields.  opts (NULL = defaults) applies to every
+ * solve; stats (NULL or count entries) receives each solve's statistics,
+ * ms being the wall time of the whole batch.  The graph is captured on the
+ * first call and relaunched while the pointers and options stay the same.
+ * Launched on cuda_stream (NULL = legacy default stream); synchronises it.
+ * Returns the first non-OK status of the solves, PLC_OK if all converged. */
+plc_status plc_batch_map(plc_batch* batch, const int32_t* const* N, const double* const* w,
+                         const double* nbar, double* const* s_inout, const plc_opts* opts,
+                         plc_stats* stats, void* cuda_stream);
+
+plc_status plc_batch_destroy(plc_batch* batch);
 
 /* Per-kernel launch counters and device time (an aid to profiling; the
  * paper has no counterpart).  Launch counts are always kept.  on != 0 also

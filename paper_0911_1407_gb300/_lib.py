@@ -25,6 +25,7 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
+           "plc_batch_create", "plc_batch_map", "plc_batch_destroy",
            "plc_profile_enable", "plc_profile_read", "plc_hessvec_noalloc", "plc_last_error",
            "plc_status_string"]
 
@@ -39,7 +40,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_newton", ctypes.c_int), ("max_cg", ctypes.c_int),
                 ("precond", ctypes.c_int), ("g0_norm", ctypes.c_double),
                 ("step_cap", ctypes.c_double), ("eta_max", ctypes.c_double),
-                ("cg_chunk", ctypes.c_int), ("mixed_switch", ctypes.c_double)]
+                ("cg_chunk", ctypes.c_int), ("mixed_switch", ctypes.c_double),
+                ("device_driven", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -47,7 +49,8 @@ class Stats(ctypes.Structure):
                 ("hv_count", ctypes.c_int), ("grad_evals", ctypes.c_int),
                 ("grad_ffts", ctypes.c_int), ("grad_ffts_fp64", ctypes.c_int),
                 ("grad_rel", ctypes.c_double), ("g0_norm", ctypes.c_double),
-                ("neg_logpost", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("neg_logpost", ctypes.c_double), ("ms", ctypes.c_double),
+                ("kernels", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -81,6 +84,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_default_opts": (I, [ctypes.POINTER(Opts)]),
         "plc_newton_krylov_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I]),
+        "plc_batch_map": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), DP, ctypes.POINTER(P),
+                              ctypes.POINTER(Opts), ctypes.POINTER(Stats), P]),
+        "plc_batch_destroy": (I, [P]),
         "plc_profile_enable": (I, [P, I]),
         "plc_profile_read": (I, [P, ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]),
         "plc_hessvec_noalloc": (I, [I, D, DP, DP, I, D, P, P, D, P, P, P]),
@@ -262,3 +269,52 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return vjp_N, vjp_lnA.value, stt.as_dict()
+
+
+class Batch:
+    """plc_batch: independent MAP solves of several contexts as one graph launch."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        self._h = ctypes.c_void_p()
+        st = self.lib.plc_batch_create(ctypes.byref(self._h), arr, len(self.contexts))
+        if st != 0:
+            raise PlcError(st, self.lib.plc_last_error(None).decode())
+
+    def close(self):
+        if self._h:
+            self.lib.plc_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def map(self, N, w, nbar, s, stream: Optional[torch.cuda.Stream] = None,
+            raise_on_fail: bool = True, **opts):
+        """Solve every context i from s[i] (float64, overwritten by its MAP)
+        with counts N[i] (int32), selection w[i] (float64 or None), nbar[i]."""
+        m = len(self.contexts)
+        if not (len(N) == len(nbar) == len(s) == m) or (w is not None and len(w) != m):
+            raise ValueError("one N, w, nbar, s per context")
+        Np = (ctypes.c_void_p * m)(*[_ptr(N[i], c.n, torch.int32, "N").value
+                                     for i, c in enumerate(self.contexts)])
+        wp = None
+        if w is not None:
+            wp = (ctypes.c_void_p * m)(*[(_ptr(w[i], c.n, torch.float64, "w", False) or
+                                          ctypes.c_void_p()).value
+                                         for i, c in enumerate(self.contexts)])
+        sp = (ctypes.c_void_p * m)(*[_ptr(s[i], c.n, torch.float64, "s").value
+                                     for i, c in enumerate(self.contexts)])
+        nb = (ctypes.c_double * m)(*[float(x) for x in nbar])
+        o, stt = default_opts(**opts), (Stats * m)()
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        st = self.lib.plc_batch_map(self._h, Np, wp, nb, sp, ctypes.byref(o), stt,
+                                    ctypes.c_void_p(stream.cuda_stream))
+        if raise_on_fail and st != 0:
+            raise PlcError(st, self.lib.plc_last_error(None).decode())
+        return st, [x.as_dict() for x in stt]

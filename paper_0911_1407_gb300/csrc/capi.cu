@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "graph.h"
 #include "solver.h"
 
 namespace {
@@ -81,6 +82,7 @@ template <typename T> void dalloc(T** p, size_t bytes) {
 }
 
 void release(plc_ctx* c) {
+  plc::graph_release(c);
   plc::profile_release(c);
   void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->M64, c->M32, c->lk, c->lP,
                   c->sc, c->partials};
@@ -140,6 +142,8 @@ plc_status check_opts(plc_ctx* c, const plc_opts& o) {
     return fail(c, PLC_ERR_INVALID_ARG, "bad step_cap / eta_max / g0_norm");
   if (o.cg_chunk < 1) return fail(c, PLC_ERR_INVALID_ARG, "opts.cg_chunk must be >= 1");
   if (!(o.mixed_switch >= 0.0)) return fail(c, PLC_ERR_INVALID_ARG, "opts.mixed_switch must be >= 0");
+  if (o.device_driven != 0 && o.device_driven != 1)
+    return fail(c, PLC_ERR_INVALID_ARG, "opts.device_driven must be 0 or 1");
   return PLC_OK;
 }
 
@@ -178,6 +182,7 @@ plc_status plc_default_opts(plc_opts* o) {
   o->eta_max = 0.5;
   o->cg_chunk = 8;
   o->mixed_switch = 1e-6;
+  o->device_driven = 1;
   return PLC_OK;
 }
 
@@ -367,10 +372,14 @@ plc_status plc_newton_krylov_map(plc_ctx* c, const int32_t* N, const void* w, do
   return guarded(c, [&]() -> plc_status {
     ensure_work_fields(c);
     plc_status st;
-    if (c->precision == PLC_FP64)
-      st = plc::newton_map<double>(c, N, static_cast<const double*>(w), nbar, s_inout, o, stats);
+    const double* wd = static_cast<const double*>(w);
+    if (o.device_driven)
+      st = c->precision == PLC_FP64
+               ? plc::newton_map_graph<double>(c, N, wd, nbar, s_inout, o, stats)
+               : plc::newton_map_graph<float>(c, N, wd, nbar, s_inout, o, stats);
     else
-      st = plc::newton_map<float>(c, N, static_cast<const double*>(w), nbar, s_inout, o, stats);
+      st = c->precision == PLC_FP64 ? plc::newton_map<double>(c, N, wd, nbar, s_inout, o, stats)
+                                    : plc::newton_map<float>(c, N, wd, nbar, s_inout, o, stats);
     if (st == PLC_ERR_NOT_CONVERGED) fail(c, st, "Newton iteration cap reached");
     else if (st == PLC_ERR_NONFINITE) fail(c, st, "non-finite gradient or objective");
     else if (st == PLC_ERR_CG_BREAKDOWN) fail(c, st, "CG breakdown on the first step");
@@ -402,6 +411,59 @@ plc_status plc_map_vjp(plc_ctx* c, const double* s_map, const void* w, double nb
     else c->err.clear();
     return st;
   });
+}
+
+struct plc_batch {
+  std::vector<plc_ctx*> ctxs;
+  plc::BatchGraph graph;
+};
+
+plc_status plc_batch_create(plc_batch** out, plc_ctx* const* ctxs, int count) {
+  if (!out) return fail(nullptr, PLC_ERR_INVALID_ARG, "batch out-pointer is NULL");
+  *out = nullptr;
+  if (!ctxs || count < 1) return fail(nullptr, PLC_ERR_INVALID_ARG, "need count >= 1 contexts");
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return fail(nullptr, PLC_ERR_INVALID_ARG, "NULL context in batch");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(nullptr, PLC_ERR_INVALID_ARG, "context repeated in batch");
+  }
+  plc_batch* b = new (std::nothrow) plc_batch();
+  if (!b) return fail(nullptr, PLC_ERR_OOM, "host allocation failed");
+  b->ctxs.assign(ctxs, ctxs + count);
+  *out = b;
+  return PLC_OK;
+}
+
+plc_status plc_batch_map(plc_batch* b, const int32_t* const* N, const double* const* w,
+                         const double* nbar, double* const* s_inout, const plc_opts* opts,
+                         plc_stats* stats, void* stream) {
+  if (!b) return fail(nullptr, PLC_ERR_INVALID_ARG, "batch is NULL");
+  if (!N || !nbar || !s_inout) return fail(nullptr, PLC_ERR_INVALID_ARG, "NULL array argument");
+  const plc_opts o = resolve_opts(opts);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    plc_ctx* c = b->ctxs[i];
+    PLC_TRY(need_prior(c));
+    PLC_TRY(need_field(c, N[i], "N", true));
+    PLC_TRY(need_field(c, w ? w[i] : nullptr, "w", false));
+    PLC_TRY(need_field(c, s_inout[i], "s_inout", true));
+    if (!(nbar[i] > 0.0) || !std::isfinite(nbar[i])) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+    PLC_TRY(check_opts(c, o));
+  }
+  plc_ctx* c0 = b->ctxs[0];
+  return guarded(c0, [&]() -> plc_status {
+    for (plc_ctx* c : b->ctxs) ensure_work_fields(c);
+    // the contexts' own streams must be idle before the batch graph runs
+    for (plc_ctx* c : b->ctxs) plc::check(cudaStreamSynchronize(c->stream), "stream synchronize");
+    const plc_status st = plc::batch_map(&b->graph, b->ctxs, N, w, nbar, s_inout, o, stats,
+                                         static_cast<cudaStream_t>(stream));
+    if (st != PLC_OK) fail(nullptr, st, "a solve of the batch did not converge");
+    return st;
+  });
+}
+
+plc_status plc_batch_destroy(plc_batch* b) {
+  delete b;
+  return PLC_OK;
 }
 
 plc_status plc_profile_enable(plc_ctx* c, int on) {

@@ -74,6 +74,12 @@ struct DevScalars {
   int iter;                  // CG iterations of the current solve
   int done, breakdown;
   unsigned ticket;           // last-block-done counter
+  // CG stopping parameters set on the device (device-driven solve): used by
+  // the CG update when it is launched with rtol2 < 0
+  double rtol2;
+  int max_iter;
+  // step length of the next Newton trial (device-driven solve)
+  double tau;
 };
 
 template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {

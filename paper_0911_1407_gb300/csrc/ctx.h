@@ -78,6 +78,9 @@ struct plc_ctx {
   plc::Profiler prof;
   std::string err;
 
+  // Device-driven solve: control block and the cached graph (graph.cu).
+  void* graph = nullptr;
+
   size_t n3() const { return (size_t)n * n * n; }
 };
 
@@ -107,12 +110,14 @@ void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, dou
 template <typename T, typename TC>
 void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,
-                   bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2);
+                   bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2,
+                   const double* tau_dev = nullptr);   // non-null: tau read on the device
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac);
 template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL* lam);
 
 // Element-wise kernels.
 template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC* r, bool jac);
+// rtol2 < 0: the stopping parameters are read from the device scalars.
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
                                       const TC* D, bool jac, double rtol2, int max_iter);
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D);

@@ -14,7 +14,7 @@ template void grad_newton<float, float, float>(plc_ctx*, const float*, const dou
 template void newton_update<float, float>(plc_ctx*, const float*, const float*, const float*,
                                           const float*, const float*, const float*,
                                           const int32_t*, const double*, double, double, bool,
-                                          float*, float*, float*, float*, float*);
+                                          float*, float*, float*, float*, float*, const double*);
 template void cg_hv<float>(plc_ctx*, const float*, const float*, float*, float*, bool);
 template void vjp_amplitude<float>(plc_ctx*, const double*, const float*);
 template void cg_init<float>(plc_ctx*, const double*, const float*, float*, bool);

@@ -17,11 +17,13 @@ template void grad_newton<double, double, float>(plc_ctx*, const double*, const 
 template void newton_update<double, double>(plc_ctx*, const double*, const double*, const double*,
                                             const double*, const double*, const double*,
                                             const int32_t*, const double*, double, double, bool,
-                                            double*, double*, double*, double*, double*);
+                                            double*, double*, double*, double*, double*,
+                                            const double*);
 template void newton_update<double, float>(plc_ctx*, const double*, const double*, const double*,
                                            const float*, const float*, const float*,
                                            const int32_t*, const double*, double, double, bool,
-                                           double*, double*, double*, float*, float*);
+                                           double*, double*, double*, float*, float*,
+                                           const double*);
 template void cg_hv<double>(plc_ctx*, const double*, const double*, double*, double*, bool);
 template void vjp_amplitude<double>(plc_ctx*, const double*, const double*);
 template void cg_init<double>(plc_ctx*, const double*, const double*, double*, bool);

@@ -183,10 +183,10 @@ template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, con
 template <typename T, typename TC>
 void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,
-                   bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2) {
+                   bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2, const double* tau_dev) {
   LaunchScope ls(c, sizeof(T) == 4 ? S_NEWTON_UPDATE32 : S_NEWTON_UPDATE64);
   k_newton_update<T, TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(
-      s, y, g, r, xi, D, N, w, nbar, c->mu, tau, c->jac_c, jac ? 1 : 0, s2, y2, g2, D2, r2,
+      s, y, g, r, xi, D, N, w, nbar, c->mu, tau, tau_dev, c->jac_c, jac ? 1 : 0, s2, y2, g2, D2, r2,
       c->n3(), red_args(c));
   check(cudaGetLastError(), "k_newton_update");
 }

@@ -392,12 +392,14 @@ k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
     double rtol2;
     int max_iter;
     __device__ void operator()(const double* t, DevScalars* sc) const {
+      const double rt2 = rtol2 < 0.0 ? sc->rtol2 : rtol2;
+      const int mi = rtol2 < 0.0 ? sc->max_iter : max_iter;
       sc->beta = t[0] / sc->rz;
       sc->rz = t[0];
       sc->rr = t[1];
       sc->xmax = t[2];
       sc->iter += 1;
-      if (t[1] <= rtol2 * sc->bnorm2 || sc->iter >= max_iter) sc->done = 1;
+      if (t[1] <= rt2 * sc->bnorm2 || sc->iter >= mi) sc->done = 1;
     }
   };
   block_reduce_finish<3, 1u << 2>(acc, ra, Fin{rtol2, max_iter});
@@ -416,13 +418,15 @@ __global__ void __launch_bounds__(kThreads)
 k_newton_update(const T* __restrict__ s, const T* __restrict__ y, const T* __restrict__ g,
                 const TC* __restrict__ r, const TC* __restrict__ xi, const TC* __restrict__ D,
                 const int32_t* __restrict__ N, const double* __restrict__ w, double nbar,
-                double mu, double tau, double c, int jac, T* __restrict__ s2,
+                double mu, double tau_arg, const double* __restrict__ tau_dev, double c,
+                int jac, T* __restrict__ s2,
                 T* __restrict__ y2, T* __restrict__ g2, TC* __restrict__ D2,
                 TC* __restrict__ r2, size_t n3, RedArgs ra) {
   using Acc = typename AccOf<T>::type;
   Acc acc[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) acc[j].init(false);
+  const double tau = tau_dev ? *tau_dev : tau_arg;
   const T tt = (T)tau, nb = (T)nbar, m = (T)mu;
   const TC cc = (TC)c;
   const size_t step = (size_t)gridDim.x * blockDim.x * 4;

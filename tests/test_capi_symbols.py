@@ -58,3 +58,19 @@ def test_validation_without_gpu(lib):
     o = Opts()
     assert lib.plc_default_opts(ctypes.byref(o)) == 0
     assert o.tol == 1e-6 and o.precond == 1 and o.max_cg == 1000
+    assert o.device_driven == 1 and o.mixed_switch == 1e-6
+
+
+def test_batch_validation_without_gpu(lib):
+    b = ctypes.c_void_p()
+    P = ctypes.c_void_p
+    lib.plc_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int]
+    assert lib.plc_batch_create(None, None, 1) == 1
+    assert lib.plc_batch_create(ctypes.byref(b), None, 1) == 1
+    arr = (P * 2)(None, None)
+    assert lib.plc_batch_create(ctypes.byref(b), arr, 2) == 1     # NULL context
+    assert lib.plc_batch_create(ctypes.byref(b), arr, 0) == 1     # empty batch
+    lib.plc_batch_map.argtypes = [P] * 8
+    assert lib.plc_batch_map(None, None, None, None, None, None, None, None) == 1
+    lib.plc_batch_destroy.argtypes = [P]
+    assert lib.plc_batch_destroy(None) == 0
