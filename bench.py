@@ -41,11 +41,14 @@ METRIC = ("256³ time-to-MAP (‖g‖/‖g0‖<1e-6) & Hv/s; mixed vs FP64 GPU, 
 UNIT = "MAP/s"
 WORKLOAD = "production256"
 TOL = 1e-6
-# Hessian-vector products and gradients of one Newton-Krylov MAP solve on this
-# workload in FP64 (the oracle's precision), used to scale the oracle's timed
-# sample (one Hv and one gradient) to MAP/s.  Same iteration as the oracle.
-REF_HV_PER_MAP = None      # filled from the FP64 GPU solve when both arms run
-REF_GRAD_PER_MAP = None
+# Work of one FP64 Newton-Krylov MAP solve of this workload, used to scale
+# the oracle's timed sample (one Hv, one gradient + objective) to MAP/s.  The
+# oracle takes the FP64 GPU solve's steps (12 Newton steps, 31 CG iterations,
+# 13 gradient evaluations with the line-search trials); it applies one more
+# Hv per Newton step for xi^T H xi of Eq. (New5) and evaluates every trial
+# through the FFT: 31 + 12 = 43 Hv and 13 gradient + objective evaluations.
+REF_HV_PER_MAP = 43
+REF_GRAD_PER_MAP = 13
 
 
 def peaks():
@@ -75,7 +78,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -197,8 +200,8 @@ def time_oracle_sample(m, repeats: int = 1):
 def reference_arm(args):
     from paper_0911_1407_gb300 import mocks
     m = mocks.make_mock(mocks.WORKLOADS[WORKLOAD])
-    hv_per_map = REF_HV_PER_MAP or 200
-    grad_per_map = REF_GRAD_PER_MAP or 15
+    hv_per_map = REF_HV_PER_MAP
+    grad_per_map = REF_GRAD_PER_MAP
     for _ in range(args.warmup):
         time_oracle_sample(m)
     times = []
@@ -234,6 +237,9 @@ def main(argv=None):
                     help="skip the FP64 solve, Hv/s sweeps and the CPU baseline")
     ap.add_argument("--micro", choices=["hv32", "hv64", "grad32", "grad64", "map32", "map64"],
                     help="profiling aid: run --reps single operator calls at size --n and exit")
+    ap.add_argument("--host-driven", action="store_true",
+                    help="run every solve with the host driver instead of one graph launch "
+                         "(same kernels; for profilers that cannot see into conditional graphs)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
@@ -270,9 +276,11 @@ def main(argv=None):
     N_dev = torch.from_numpy(m.N).cuda()
     s = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
 
+    driven = 0 if args.host_driven else 1
+
     def step():
         s.fill_(m.mu)
-        return ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL)
+        return ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, device_driven=driven)
 
     for _ in range(args.warmup):
         step()
@@ -295,7 +303,9 @@ def main(argv=None):
     clk = clocks.stop()
     t_dev = e0.elapsed_time(e1) / 1e3
     # each solve is one graph launch; the library counts the kernels it ran
-    launches = int(sum(st["kernels"] for st in stats))
+    # (the host driver's launches are counted by the profiling counters)
+    launches = (int(sum(v[0] for v in ctx.profile_read().values())) if args.host_driven
+                else int(sum(st["kernels"] for st in stats)))
     if world > 1:
         t = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -441,7 +451,8 @@ def micro(args):
             c.logpost_grad(s, N, None, 1.0, grad=out)
         else:
             s64.fill_(-1.62)
-            c.newton_krylov_map(N, None, 1.0, s=s64, tol=1e-6, raise_on_fail=False)
+            c.newton_krylov_map(N, None, 1.0, s=s64, tol=1e-6, raise_on_fail=False,
+                                device_driven=0 if args.host_driven else 1)
     e1.record()
     torch.cuda.synchronize()
     print(json.dumps({"micro": args.micro, "n": n, "reps": args.reps,
@@ -523,12 +534,15 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:
         t_hv, t_g = time_oracle_sample(m)
-        hvc, gc = r.stats["hv_count"], r.stats["grad_evals"]
+        # the oracle's own iteration: the FP64 solve's CG products plus one Hv
+        # per Newton step for Eq. (New5), every trial through the FFT
+        hvc = r.stats["hv_count"] + r.stats["newton_iters"]
+        gc = r.stats["grad_evals"]
         t_map = t_hv * hvc + t_g * gc
         line["cpu_baseline"] = {
             "value": 1.0 / t_map, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"one oracle Hv ({t_hv:.2f} s) and one gradient+objective ({t_g:.2f} s) at "
-                       f"256^3, scaled by the FP64 solve's {hvc} Hv and {gc} gradients per MAP"),
+                       f"256^3, scaled to the oracle's {hvc} Hv and {gc} gradients per MAP"),
             "hv_per_s": 1.0 / t_hv}
 
 
@@ -545,6 +559,13 @@ def batch_extra(plc, line):
         c = plc.Context(m.n, m.box, "mixed")
         c.set_prior(m.k_tab, m.P_tab, m.mu)
         cs.append(c)
+    # FFT schedule per grid size: autotuned on the first context of each size
+    schedules = {}
+    for c in cs:
+        if c.n not in schedules:
+            f1, f2, us = c.autotune(reps=20)
+            schedules[c.n] = {"f1": f1, "f2": f2, "us_per_hv": us}
+        c.set_fft_schedule(schedules[c.n]["f1"], schedules[c.n]["f2"])
     Ns = [torch.from_numpy(m.N).cuda() for m in ms]
     ss = [torch.empty((m.n,) * 3, dtype=torch.float64, device="cuda") for m in ms]
     nb = [m.nbar for m in ms]
@@ -585,7 +606,8 @@ def batch_extra(plc, line):
         "newton_iters": sum(st["newton_iters"] for st in stats),
         "cg_iters": sum(st["cg_iters"] for st in stats),
         "kernels": sum(st["kernels"] for st in stats),
-        "max_grad_rel": max(st["grad_rel"] for st in stats)}
+        "max_grad_rel": max(st["grad_rel"] for st in stats),
+        "fft_schedules": {str(k): v for k, v in schedules.items()}}
     del b, cs
 
 

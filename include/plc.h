@@ -166,6 +166,21 @@ plc_status plc_map_vjp(plc_ctx* ctx, const double* s_map, const void* w,
                        double nbar, const double* u, double* vjp_N,
                        double* vjp_lnA, const plc_opts* opts, plc_stats* stats);
 
+/* FFT schedule of the FP32 transforms (PLC_MIXED contexts; an aid to
+ * performance, the paper has no counterpart).  A length n = f1 f2 with a
+ * register four-step form can run it with the factors (f1, f2) or with the
+ * shared-memory Stockham stages (f1 = f2 = 0); every schedule computes the
+ * same transform.  plc_set_fft_schedule selects one (INVALID_ARG if (f1, f2)
+ * is not offered for this n).  plc_autotune times `reps` (1..1000)
+ * Hessian-vector products with each schedule offered for n, keeps the
+ * fastest and returns it (f1, f2 and its time per Hv in microseconds, any
+ * output may be NULL); it uses the solver work fields as scratch (and
+ * allocates them on first use) and synchronises the stream.  On a PLC_FP64
+ * context (Stockham only) it times nothing and returns the current
+ * schedule with *us_per_hv = 0. */
+plc_status plc_set_fft_schedule(plc_ctx* ctx, int f1, int f2);
+plc_status plc_autotune(plc_ctx* ctx, int reps, int* f1, int* f2, double* us_per_hv);
+
 /* A batch of independent MAP solves (many mocks, each with its own grid
  * size, prior, counts and selection; the paper has no counterpart): every
  * context's device-driven solve is captured as its own chain of one CUDA

@@ -25,6 +25,7 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
+           "plc_set_fft_schedule", "plc_autotune",
            "plc_batch_create", "plc_batch_map", "plc_batch_destroy",
            "plc_profile_enable", "plc_profile_read", "plc_hessvec_noalloc", "plc_last_error",
            "plc_status_string"]
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_default_opts": (I, [ctypes.POINTER(Opts)]),
         "plc_newton_krylov_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_set_fft_schedule": (I, [P, I, I]),
+        "plc_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), DP]),
         "plc_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I]),
         "plc_batch_map": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), DP, ctypes.POINTER(P),
                               ctypes.POINTER(Opts), ctypes.POINTER(Stats), P]),
@@ -244,6 +247,18 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return MapResult(s, st, stt.as_dict())
+
+    def set_fft_schedule(self, f1: int, f2: int):
+        """FP32 line-transform schedule: four-step n = f1 f2, or (0, 0) Stockham."""
+        self._check(self.lib.plc_set_fft_schedule(self._h, int(f1), int(f2)))
+
+    def autotune(self, reps: int = 20):
+        """Time every FP32 schedule offered for n, keep the fastest; returns
+        (f1, f2, microseconds per Hv)."""
+        f1, f2, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.plc_autotune(self._h, int(reps), ctypes.byref(f1), ctypes.byref(f2),
+                                          ctypes.byref(us)))
+        return f1.value, f2.value, us.value
 
     def profile_enable(self, timing: bool = True):
         """Reset the per-kernel counters; timing=True also times every launch."""

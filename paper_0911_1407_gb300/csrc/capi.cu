@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ctx.h"
@@ -61,14 +62,15 @@ plc::FftPlan make_plan(int n) {
     ns *= r[i];
   }
   p.nd = plc::make_fastdiv(n);
-  // FP32 transforms of these lengths use the register-resident four-step
-  // form n = f1 f2 (see fft_tile)
-  struct Pair { int n, f1, f2; };
-  const Pair fs[] = {{256, 16, 16}, {192, 16, 12}, {128, 16, 8}, {96, 12, 8}, {64, 8, 8}, {32, 8, 4}};
+  // FP32 transforms of these lengths use a register four-step schedule
+  // n = f1 f2 (passes4.cuh); the first listed for n is the default
   p.f1 = p.f2 = 0;
-  for (const Pair& q : fs)
-    if (q.n == n) { p.f1 = q.f1; p.f2 = q.f2; }
-  p.f1d = plc::make_fastdiv(p.f1 ? p.f1 : 2);
+  for (const plc::FourStepShape& q : plc::kFourStep)
+    if (q.n == n) {
+      p.f1 = q.f1;
+      p.f2 = q.f2;
+      break;
+    }
   return p;
 }
 
@@ -410,6 +412,73 @@ plc_status plc_map_vjp(plc_ctx* c, const double* s_map, const void* w, double nb
     if (st != PLC_OK) fail(c, st, "adjoint CG did not reach the tolerance");
     else c->err.clear();
     return st;
+  });
+}
+
+plc_status plc_set_fft_schedule(plc_ctx* c, int f1, int f2) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  bool ok = f1 == 0 && f2 == 0;
+  for (const plc::FourStepShape& q : plc::kFourStep)
+    if (q.n == c->n && q.f1 == f1 && q.f2 == f2) ok = true;
+  if (!ok) return fail(c, PLC_ERR_INVALID_ARG, "no such FFT schedule for this grid size");
+  c->plan.f1 = f1;
+  c->plan.f2 = f2;
+  return PLC_OK;
+}
+
+plc_status plc_autotune(plc_ctx* c, int reps, int* f1_out, int* f2_out, double* us_out) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  if (reps < 1 || reps > 1000) return fail(c, PLC_ERR_INVALID_ARG, "reps must be 1..1000");
+  PLC_TRY(need_prior(c));
+  return guarded(c, [&]() -> plc_status {
+    double best_us = 0.0;
+    if (c->precision == PLC_MIXED) {
+      ensure_work_fields(c);
+      float* s = static_cast<float*>(c->wf[0]);
+      float* v = static_cast<float*>(c->wf[1]);
+      float* out = static_cast<float*>(c->wf[2]);
+      const size_t bytes = sizeof(float) * c->n3();
+      plc::check(cudaMemsetAsync(s, 0, bytes, c->stream), "clear");
+      plc::check(cudaMemsetAsync(v, 0, bytes, c->stream), "clear");
+      std::vector<std::pair<int, int>> cand{{0, 0}};
+      for (const plc::FourStepShape& q : plc::kFourStep)
+        if (q.n == c->n) cand.emplace_back(q.f1, q.f2);
+      cudaEvent_t e0, e1;
+      plc::check(cudaEventCreate(&e0), "event");
+      plc::check(cudaEventCreate(&e1), "event");
+      std::pair<int, int> best{c->plan.f1, c->plan.f2};
+      best_us = -1.0;
+      try {
+        for (const auto& f : cand) {
+          c->plan.f1 = f.first;
+          c->plan.f2 = f.second;
+          plc::hessvec_s<float>(c, s, nullptr, 1.0, v, out);   // warm-up
+          plc::check(cudaEventRecord(e0, c->stream), "event");
+          for (int i = 0; i < reps; ++i) plc::hessvec_s<float>(c, s, nullptr, 1.0, v, out);
+          plc::check(cudaEventRecord(e1, c->stream), "event");
+          plc::check(cudaEventSynchronize(e1), "event");
+          float ms = 0.f;
+          plc::check(cudaEventElapsedTime(&ms, e0, e1), "event");
+          const double us = 1e3 * ms / reps;
+          if (best_us < 0.0 || us < best_us) {
+            best_us = us;
+            best = f;
+          }
+        }
+      } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->plan.f1 = best.first;
+      c->plan.f2 = best.second;
+    }
+    if (f1_out) *f1_out = c->plan.f1;
+    if (f2_out) *f2_out = c->plan.f2;
+    if (us_out) *us_out = best_us;
+    return PLC_OK;
   });
 }
 

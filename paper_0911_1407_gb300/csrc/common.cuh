@@ -47,18 +47,9 @@ struct FftPlan {
   int tstep[kMaxStages];     // twiddle index step n / (ns * rad)
   unsigned ns_m[kMaxStages]; // fast-division multiplier for ns (0 when ns = 1)
   FastDiv nd;                // division by n
-  int f1, f2;                // four-step factors n = f1 f2 (0 = use the Stockham stages)
-  FastDiv f1d;               // division by f1
+  int f1, f2;                // FP32 register four-step factors n = f1 f2
+                             // (0 = the Stockham stages)
 };
-
-// Slot of frequency (or, after an inverse, position) k in a line left by the
-// four-step transform in transposed order; identity for the Stockham stages.
-// `four_step` says which of the two produced the line.
-__device__ __forceinline__ int fft_slot(const FftPlan& p, bool four_step, int k) {
-  if (!four_step) return k;
-  const int q = (int)fdiv((unsigned)k, p.f1d);
-  return (k - q * p.f1) * p.f2 + q;
-}
 
 // Device-resident scalars of the solver (one instance per context).
 struct DevScalars {
@@ -198,7 +189,8 @@ __device__ __forceinline__ void fft_lines(cpx<T>*& a, cpx<T>*& b, const FftPlan&
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident small DFTs and the four-step line FFT.
+// Register-resident small DFTs (the building blocks of the four-step line
+// transforms in passes4.cuh).
 //
 // exp(2 pi i m / R) for the radices used in registers (R in {2,3,4,6,8,12,16});
 // after unrolling m and R are constants and the switch folds away.
@@ -281,146 +273,6 @@ __device__ __forceinline__ void dft_small(cpx<T>* v) {
       for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
     }
   }
-}
-
-// Four-step line FFT of length N = N1 N2 on `nl` (<= L) lines held in
-// shared memory (element i of line c at buf[i * P + c]), in place.
-// X[k1 + N1 k2] = sum_n2 W_N2^{n2 k2} W_N^{n2 k1} sum_n1 x[N2 n1 + n2] W_N1^{n1 k1}.
-// Phase A (task (c, n2)): DFT_N1 over n1, twiddle, back to the same slots
-// {m N2 + n2}; phase B (task (c, k1)): DFT_N2 over n2, back to the same slots
-// {k1 N2 + m}.  Each task rewrites exactly the slots it read, so a phase
-// needs no barrier inside; one barrier separates the phases.  The result is
-// left in transposed order: X[k1 + N1 k2] at slot k1 N2 + k2.
-// tw[m] = exp(-2 pi i m / N).  Enter after a barrier; ends with one.
-template <typename T, int SIGN, int N1, int N2>
-__device__ __forceinline__ void fft4_phase_a(cpx<T>* buf, int L, int nl, int P,
-                                             const cpx<T>* __restrict__ tw) {
-  using C = cpx<T>;
-  for (int t = threadIdx.x; t < L * N2; t += blockDim.x) {
-    const int c = t % L, n2 = t / L;
-    if (c >= nl) continue;
-    C v[N1];
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) v[n1] = buf[(N2 * n1 + n2) * P + c];
-    dft_small<T, SIGN, N1>(v);
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      if (k1 > 0 && n2 > 0) {
-        C w = tw[n2 * k1];
-        if (SIGN > 0) w.y = -w.y;
-        v[k1] = cmul(v[k1], w);
-      }
-      buf[(k1 * N2 + n2) * P + c] = v[k1];
-    }
-  }
-}
-
-template <typename T, int SIGN, int N1, int N2>
-__device__ __forceinline__ void fft4_phase_b(cpx<T>* buf, int L, int nl, int P) {
-  using C = cpx<T>;
-  for (int t = threadIdx.x; t < L * N1; t += blockDim.x) {
-    const int c = t % L, k1 = t / L;
-    if (c >= nl) continue;
-    C v[N2];
-#pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[(k1 * N2 + n2) * P + c];
-    dft_small<T, SIGN, N2>(v);
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) buf[(k1 * N2 + k2) * P + c] = v[k2];
-  }
-}
-
-template <typename T, int SIGN, int N1, int N2>
-__device__ __forceinline__ void fft4(cpx<T>* buf, int L, int nl, int P, const cpx<T>* tw) {
-  fft4_phase_a<T, SIGN, N1, N2>(buf, L, nl, P, tw);
-  __syncthreads();
-  fft4_phase_b<T, SIGN, N1, N2>(buf, L, nl, P);
-  __syncthreads();
-}
-
-// Inverse four-step transform from the transposed order left by fft4
-// (frequency k1 + N1 k2 at slot k1 N2 + k2) to natural order, unnormalised:
-// phase B' (inverse DFT_N2 over k2, conjugate twiddle) then phase A'
-// (inverse DFT_N1 over k1).  Enter after a barrier; ends with one.
-template <typename T, int N1, int N2>
-__device__ __forceinline__ void fft4_inverse_t(cpx<T>* buf, int L, int nl, int P,
-                                               const cpx<T>* __restrict__ tw) {
-  using C = cpx<T>;
-  for (int t = threadIdx.x; t < L * N1; t += blockDim.x) {
-    const int c = t % L, k1 = t / L;
-    if (c >= nl) continue;
-    C v[N2];
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) v[k2] = buf[(k1 * N2 + k2) * P + c];
-    dft_small<T, +1, N2>(v);
-#pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) {
-      if (k1 > 0 && n2 > 0) {
-        C w = tw[n2 * k1];
-        w.y = -w.y;
-        v[n2] = cmul(v[n2], w);
-      }
-      buf[(k1 * N2 + n2) * P + c] = v[n2];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < L * N2; t += blockDim.x) {
-    const int c = t % L, n2 = t / L;
-    if (c >= nl) continue;
-    C v[N1];
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) v[k1] = buf[(k1 * N2 + n2) * P + c];
-    dft_small<T, +1, N1>(v);
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) buf[(N2 * n1 + n2) * P + c] = v[n1];
-  }
-  __syncthreads();
-}
-
-// Forward transform, pointwise multiply by mul(c, k) (k = frequency index),
-// inverse transform (unnormalised), in place; the result is in natural
-// order.  The spectrum of each phase-B task stays in registers between the
-// two transforms.
-template <typename T, int N1, int N2, typename Mul>
-__device__ __forceinline__ void fft4_filter(cpx<T>* buf, int L, int nl, int P, const cpx<T>* tw,
-                                            Mul mul) {
-  using C = cpx<T>;
-  constexpr int N = N1 * N2;
-  fft4_phase_a<T, -1, N1, N2>(buf, L, nl, P, tw);
-  __syncthreads();
-  for (int t = threadIdx.x; t < L * N1; t += blockDim.x) {
-    const int c = t % L, k1 = t / L;
-    if (c >= nl) continue;
-    C v[N2];
-#pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[(k1 * N2 + n2) * P + c];
-    dft_small<T, -1, N2>(v);
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) v[k2] = cscale(v[k2], mul(c, k1 + N1 * k2));
-    dft_small<T, +1, N2>(v);
-#pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) {
-      if (k1 > 0 && n2 > 0) {
-        C w = tw[n2 * k1];
-        w.y = -w.y;
-        v[n2] = cmul(v[n2], w);
-      }
-      buf[(k1 * N2 + n2) * P + c] = v[n2];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < L * N2; t += blockDim.x) {
-    const int c = t % L, n2 = t / L;
-    if (c >= nl) continue;
-    C v[N1];
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) v[k1] = buf[(k1 * N2 + n2) * P + c];
-    dft_small<T, +1, N1>(v);
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) buf[(N2 * n1 + n2) * P + c] = v[n1];
-  }
-  __syncthreads();
-  (void)N;
 }
 
 // ---------------------------------------------------------------------------

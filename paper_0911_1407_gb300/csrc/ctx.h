@@ -27,6 +27,16 @@ enum Site {
 };
 extern const char* const kSiteNames[S_NSITES];
 
+// FP32 line-transform schedules with a register four-step form (passes4.cuh):
+// n = f1 f2.  The first entry for an n is the default; plc_autotune times
+// every entry for n and the Stockham form (f1 = f2 = 0).
+struct FourStepShape {
+  int n, f1, f2;
+};
+constexpr FourStepShape kFourStep[] = {
+    {256, 16, 16}, {192, 16, 12}, {192, 12, 16}, {128, 16, 8}, {128, 8, 16},
+    {96, 12, 8},   {96, 8, 12},   {64, 8, 8},    {32, 8, 4}};
+
 struct Profiler {
   bool timing = false;
   long long launches[S_NSITES] = {};

@@ -494,7 +494,7 @@ plc_status newton_map_graph(plc_ctx* c, const int32_t* N, const double* w, doubl
   const void* kp[3] = {N, w, s_out};
   const double kv[8] = {nbar, o.tol, o.g0_norm, o.step_cap, o.eta_max, o.mixed_switch, c->mu,
                         c->jac_c};
-  const int ki[4] = {o.max_newton, o.max_cg, o.precond, 0};
+  const int ki[4] = {o.max_newton, o.max_cg, o.precond, c->plan.f1 * 64 + c->plan.f2};
   if (!same_key(gs, kp, kv, ki)) {
     if (gs->exec) {
       cudaGraphExecDestroy(gs->exec);
@@ -547,7 +547,12 @@ plc_status batch_map(BatchGraph* b, const std::vector<plc_ctx*>& cs, const int32
   }
   std::vector<double> kv{o.tol, o.g0_norm, o.step_cap, o.eta_max, o.mixed_switch,
                          (double)o.max_newton, (double)o.max_cg, (double)o.precond};
-  for (size_t i = 0; i < m; ++i) kv.push_back(nbar[i]);
+  for (size_t i = 0; i < m; ++i) {
+    kv.push_back(nbar[i]);
+    kv.push_back(cs[i]->mu);
+    kv.push_back(cs[i]->jac_c);
+    kv.push_back((double)(cs[i]->plan.f1 * 64 + cs[i]->plan.f2));
+  }
   if (!b->exec || key != b->key || kv != b->key_val) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);

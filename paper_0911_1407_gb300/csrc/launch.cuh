@@ -69,10 +69,14 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
                                 : (sizeof(T) == 8 ? S_XF64 : S_XF32);
   if constexpr (sizeof(T) == 4) {
     switch (c->plan.f1 * 64 + c->plan.f2) {
+      // every entry of kFourStep (ctx.h)
       case 16 * 64 + 16: return run_pipeline4<16, 16>(c, pro, epi, fin, zero_dc, done, s0);
       case 16 * 64 + 12: return run_pipeline4<16, 12>(c, pro, epi, fin, zero_dc, done, s0);
+      case 12 * 64 + 16: return run_pipeline4<12, 16>(c, pro, epi, fin, zero_dc, done, s0);
       case 16 * 64 + 8: return run_pipeline4<16, 8>(c, pro, epi, fin, zero_dc, done, s0);
+      case 8 * 64 + 16: return run_pipeline4<8, 16>(c, pro, epi, fin, zero_dc, done, s0);
       case 12 * 64 + 8: return run_pipeline4<12, 8>(c, pro, epi, fin, zero_dc, done, s0);
+      case 8 * 64 + 12: return run_pipeline4<8, 12>(c, pro, epi, fin, zero_dc, done, s0);
       case 8 * 64 + 8: return run_pipeline4<8, 8>(c, pro, epi, fin, zero_dc, done, s0);
       case 8 * 64 + 4: return run_pipeline4<8, 4>(c, pro, epi, fin, zero_dc, done, s0);
       default: break;

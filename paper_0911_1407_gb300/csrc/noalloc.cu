@@ -116,7 +116,6 @@ plc::FftPlan noalloc_plan(int n) {
   }
   p.nd = plc::make_fastdiv(n);
   p.f1 = p.f2 = 0;                    // FP64: Stockham stages
-  p.f1d = plc::make_fastdiv(2);
   return p;
 }
 

@@ -17,6 +17,10 @@
 // step) and the epilogue fuses the pointwise tail (gradient of Sec. 3.1.2,
 // Hessian-vector product, dot products) into the last pass.
 //
+// These kernels serve FP64, and FP32 lengths (or schedules) without a
+// register four-step form (passes4.cuh); their line transform is a
+// mixed-radix Stockham FFT in shared memory.
+//
 // Every block has all global loads of a tile in flight at once: the pure data
 // passes (YF, Z, YI) copy their tiles with cp.async straight into shared
 // memory, and XF / XI batch their loads in registers.  In A the spectra of
@@ -34,51 +38,28 @@ template <typename T> struct PassGeom {
   static constexpr int P = L + 1;         // padded pitch of a tile row
   static constexpr int RY = 2 * L;        // real rows per x-pass tile
   static __host__ __device__ int buf_elems(int n) { return n * P; }
-  // the four-step transform (FP32 only) works in place in one line buffer;
-  // the Stockham stages ping-pong between two
-  static __host__ __device__ bool four_step(const FftPlan& p) { return sizeof(T) == 4 && p.f1; }
+  // twiddles and the two buffers the Stockham stages ping-pong between
   static __host__ __device__ size_t smem_bytes(const FftPlan& p) {
-    return sizeof(cpx<T>) * ((size_t)p.n + (four_step(p) ? 1 : 2) * (size_t)buf_elems(p.n));
+    return sizeof(cpx<T>) * ((size_t)p.n + 2 * (size_t)buf_elems(p.n));
   }
   static __host__ __device__ size_t smem_bytes_max(int n) {
     return sizeof(cpx<T>) * ((size_t)n + 2 * (size_t)buf_elems(n));
   }
 };
 
-// Forward line transform of the tile in `a`: natural order in; the result is
-// in `a` with frequency k at slot fft_slot(plan, four_step, k).
+// Forward line transform of the tile (natural order in and out); on return
+// `a` points at the result.
 template <typename T>
 __device__ __forceinline__ void fft_tile_fwd(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
                                              const cpx<T>* tw) {
-  using G = PassGeom<T>;
-  if constexpr (sizeof(T) == 4) {
-    const int f = plan.f1 * 64 + plan.f2;
-    if (f == 16 * 64 + 16) { fft4<T, -1, 16, 16>(a, G::L, nl, G::P, tw); return; }
-    if (f == 16 * 64 + 8) { fft4<T, -1, 16, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 16 * 64 + 12) { fft4<T, -1, 16, 12>(a, G::L, nl, G::P, tw); return; }
-    if (f == 12 * 64 + 8) { fft4<T, -1, 12, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 8 * 64 + 8) { fft4<T, -1, 8, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 8 * 64 + 4) { fft4<T, -1, 8, 4>(a, G::L, nl, G::P, tw); return; }
-  }
-  fft_lines<T, -1, G::L>(a, b, plan, nl, G::P, tw);
+  fft_lines<T, -1, PassGeom<T>::L>(a, b, plan, nl, PassGeom<T>::P, tw);
 }
 
-// Inverse line transform (unnormalised): frequency k at slot
-// fft_slot(plan, four_step, k) in; natural order out, in `a`.
+// Inverse line transform (unnormalised), natural order in and out.
 template <typename T>
 __device__ __forceinline__ void fft_tile_inv(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
                                              const cpx<T>* tw) {
-  using G = PassGeom<T>;
-  if constexpr (sizeof(T) == 4) {
-    const int f = plan.f1 * 64 + plan.f2;
-    if (f == 16 * 64 + 16) { fft4_inverse_t<T, 16, 16>(a, G::L, nl, G::P, tw); return; }
-    if (f == 16 * 64 + 8) { fft4_inverse_t<T, 16, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 16 * 64 + 12) { fft4_inverse_t<T, 16, 12>(a, G::L, nl, G::P, tw); return; }
-    if (f == 12 * 64 + 8) { fft4_inverse_t<T, 12, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 8 * 64 + 8) { fft4_inverse_t<T, 8, 8>(a, G::L, nl, G::P, tw); return; }
-    if (f == 8 * 64 + 4) { fft4_inverse_t<T, 8, 4>(a, G::L, nl, G::P, tw); return; }
-  }
-  fft_lines<T, +1, G::L>(a, b, plan, nl, G::P, tw);
+  fft_lines<T, +1, PassGeom<T>::L>(a, b, plan, nl, PassGeom<T>::P, tw);
 }
 
 // Forward transform, multiply by mul(line, kz), inverse transform: natural
@@ -87,15 +68,6 @@ template <typename T, typename Mul>
 __device__ __forceinline__ void filter_tile(cpx<T>*& a, cpx<T>*& b, const FftPlan& plan, int nl,
                                             const cpx<T>* tw, Mul mul) {
   using G = PassGeom<T>;
-  if constexpr (sizeof(T) == 4) {
-    const int f = plan.f1 * 64 + plan.f2;
-    if (f == 16 * 64 + 16) { fft4_filter<T, 16, 16>(a, G::L, nl, G::P, tw, mul); return; }
-    if (f == 16 * 64 + 8) { fft4_filter<T, 16, 8>(a, G::L, nl, G::P, tw, mul); return; }
-    if (f == 16 * 64 + 12) { fft4_filter<T, 16, 12>(a, G::L, nl, G::P, tw, mul); return; }
-    if (f == 12 * 64 + 8) { fft4_filter<T, 12, 8>(a, G::L, nl, G::P, tw, mul); return; }
-    if (f == 8 * 64 + 8) { fft4_filter<T, 8, 8>(a, G::L, nl, G::P, tw, mul); return; }
-    if (f == 8 * 64 + 4) { fft4_filter<T, 8, 4>(a, G::L, nl, G::P, tw, mul); return; }
-  }
   fft_lines<T, -1, G::L>(a, b, plan, nl, G::P, tw);
   const int n = plan.n;
   const FastDiv ld = make_fastdiv(nl);
@@ -191,8 +163,8 @@ k_xf(Pro pro, cpx<T>* __restrict__ A, FftPlan plan, const cpx<T>* __restrict__ t
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < h * lines; e += kThreads) {
     const int k = fdiv(e, ld), j = e - k * lines;
-    const C zk = a[fft_slot(plan, G::four_step(plan), k) * G::P + j];
-    const C zc = cconj(a[fft_slot(plan, G::four_step(plan), k ? n - k : 0) * G::P + j]);
+    const C zk = a[k * G::P + j];
+    const C zc = cconj(a[(k ? n - k : 0) * G::P + j]);
     const C s = cadd(zk, zc), d = csub(zk, zc);
     st_pair(&A[((size_t)z * h + k) * n + y0 + 2 * j], cmk<C>((T)0.5 * s.x, (T)0.5 * s.y),
             cmk<C>((T)0.5 * d.y, (T)-0.5 * d.x));
@@ -222,7 +194,7 @@ k_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, FftPlan plan,
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = fdiv(e, ld), line = e - ky * lines;
-    B[((size_t)kx * n + ky) * n + z0 + line] = a[fft_slot(plan, G::four_step(plan), ky) * G::P + line];
+    B[((size_t)kx * n + ky) * n + z0 + line] = a[ky * G::P + line];
   }
 }
 
@@ -276,7 +248,7 @@ k_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, FftPlan plan,
   const FastDiv ld = make_fastdiv(lines);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     const int ky = fdiv(e, ld), line = e - ky * lines;
-    cp_async(&a[fft_slot(plan, G::four_step(plan), ky) * G::P + line],
+    cp_async(&a[ky * G::P + line],
              &B[((size_t)kx * n + ky) * n + z0 + line]);
   }
   cp_async_wait_all();
@@ -307,7 +279,6 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
   const int lines = rows >> 1;
   const int npairs = h * lines;
   const FastDiv ld = make_fastdiv(lines);
-  const bool fs = G::four_step(plan);
   constexpr int B4 = 4;
   for (int base = threadIdx.x; base < npairs; base += B4 * kThreads) {
     C xa[B4], xb[B4];
@@ -326,9 +297,9 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
         const int k = fdiv(e, ld), j = e - k * lines;
         C va = xa[q], vb = xb[q];
         if (k == 0 || k == nh) { va.y = (T)0; vb.y = (T)0; }
-        a[fft_slot(plan, fs, k) * G::P + j] = cmk<C>(va.x - vb.y, va.y + vb.x);
+        a[k * G::P + j] = cmk<C>(va.x - vb.y, va.y + vb.x);
         if (k > 0 && k < nh)
-          a[fft_slot(plan, fs, n - k) * G::P + j] = cmk<C>(va.x + vb.y, vb.x - va.y);
+          a[(n - k) * G::P + j] = cmk<C>(va.x + vb.y, vb.x - va.y);
       }
     }
   }
