@@ -86,7 +86,7 @@ template <typename T> void dalloc(T** p, size_t bytes) {
 void release(plc_ctx* c) {
   plc::graph_release(c);
   plc::profile_release(c);
-  void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->M64, c->M32, c->lk, c->lP,
+  void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->twff, c->M64, c->M32, c->lk, c->lP,
                   c->sc, c->partials};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -213,6 +213,7 @@ plc_status plc_create(plc_ctx** out, int n, double box, int precision, void* str
     dalloc(&c->specB, spec);
     dalloc(&c->tw64, sizeof(double2) * n);
     dalloc(&c->tw32, sizeof(float2) * n);
+    dalloc(&c->twff, sizeof(float4) * n);
     dalloc(&c->sc, sizeof(plc::DevScalars));
     plc::check(cudaMallocHost(reinterpret_cast<void**>(&c->sc_host), sizeof(plc::DevScalars)),
                "cudaMallocHost");
@@ -222,13 +223,17 @@ plc_status plc_create(plc_ctx** out, int n, double box, int precision, void* str
     // twiddles W_n^m = exp(-2 pi i m / n), from the FP64 host sin/cos
     std::vector<double2> t64(n);
     std::vector<float2> t32(n);
+    std::vector<float4> tff(n);   // float-float: (re hi, re lo, im hi, im lo)
     for (int m = 0; m < n; ++m) {
       const double ang = 2.0 * M_PI * (double)m / (double)n;
       t64[m] = make_double2(std::cos(ang), -std::sin(ang));
       t32[m] = make_float2((float)t64[m].x, (float)t64[m].y);
+      tff[m] = make_float4(t32[m].x, (float)(t64[m].x - (double)t32[m].x), t32[m].y,
+                           (float)(t64[m].y - (double)t32[m].y));
     }
     plc::check(cudaMemcpyAsync(c->tw64, t64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
     plc::check(cudaMemcpyAsync(c->tw32, t32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
+    plc::check(cudaMemcpyAsync(c->twff, tff.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
     plc::check(cudaMemsetAsync(c->sc, 0, sizeof(plc::DevScalars), c->stream), "clear scalars");
     plc::check(cudaStreamSynchronize(c->stream), "stream synchronize");
     return PLC_OK;

@@ -21,6 +21,8 @@ enum Site {
   // pipelines of the Newton gradient (and line-search trials)
   S_GXF64, S_GYF64, S_GZ64, S_GYI64, S_GXI64,
   S_GXF32, S_GYF32, S_GZ32, S_GYI32, S_GXI32,
+  // the FP64 gradient of the mixed solve in float-float transforms
+  S_GXFF, S_GYFF, S_GZFF, S_GYIFF, S_GXIFF,
   S_CG_INIT, S_CG_UPDATE64, S_CG_UPDATE32, S_NEWTON_UPDATE64, S_NEWTON_UPDATE32,
   S_DIAG, S_CONVERT, S_SETUP,
   S_NSITES
@@ -62,6 +64,7 @@ struct plc_ctx {
   void* specB = nullptr;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
+  void* twff = nullptr;        // float-float twiddles (ffc, ff.cuh)
 
   // Prior: inverse eigenvalue per |m|^2, its FP32 copy, ln-tables.
   double* M64 = nullptr;

@@ -5,6 +5,8 @@
 
 #include "ctx.h"
 #include "ops.cuh"
+#include <type_traits>
+
 #include "passes.cuh"
 #include "passes4.cuh"
 
@@ -27,37 +29,74 @@ template <typename T, auto Kernel> inline void set_smem() {
 
 inline RedArgs red_args(plc_ctx* c) { return RedArgs{c->partials, c->sc}; }
 
-// The FP32 passes with register four-step line transforms (passes4.cuh).
-template <int N1, int N2, typename Pro, typename Epi, typename Fin>
+// Raise a kernel's dynamic shared-memory limit once (when above 48 KB).
+template <auto Kernel> inline void set_smem4(size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static const cudaError_t once =
+      cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  check(once, "cudaFuncSetAttribute");
+}
+
+// The passes with register four-step line transforms (passes4.cuh) in
+// transform arithmetic T: float (FP32 twiddles and multipliers) or ff
+// (float-float, from the FP64 tables).
+template <typename T, int N1, int N2, typename Pro, typename Epi, typename Fin>
 void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0) {
-  using Gm = Geo4<N1, N2>;
+  using Gm = Geo4<T, N1, N2>;
+  using C = cpx<T>;
+  constexpr bool kFF = std::is_same<T, ff>::value;
+  using TM = typename std::conditional<kFF, double, float>::type;
   constexpr int n = Gm::N, h = n / 2 + 1;
-  float2* A = static_cast<float2*>(c->specA);
-  float2* B = static_cast<float2*>(c->specB);
-  const float2* tw = c->tw32;
+  C* A = static_cast<C*>(c->specA);
+  C* B = static_cast<C*>(c->specB);
+  const C* tw = kFF ? static_cast<const C*>(c->twff) : reinterpret_cast<const C*>(c->tw32);
+  const TM* M = kFF ? reinterpret_cast<const TM*>(c->M64) : reinterpret_cast<const TM*>(c->M32);
   const dim3 gx(n / Gm::RY, n), gy(n / Gm::L, h);
+  set_smem4<k4_xf<T, N1, N2, Pro>>(Gm::smem_x);
+  set_smem4<k4_yf<T, N1, N2>>(Gm::smem_y);
+  set_smem4<k4_z<T, N1, N2, TM>>(Gm::smem_z);
+  set_smem4<k4_yi<T, N1, N2>>(Gm::smem_y);
+  set_smem4<k4_xi<T, N1, N2, Epi, Fin>>(Gm::smem_x);
   {
     LaunchScope ls(c, Site(s0 + 0));
-    k4_xf<N1, N2, Pro><<<gx, kThreads, Gm::smem_x, c->stream>>>(pro, A, tw, done);
+    k4_xf<T, N1, N2, Pro><<<gx, kThreads, Gm::smem_x, c->stream>>>(pro, A, tw, done);
   }
   {
     LaunchScope ls(c, Site(s0 + 1));
-    k4_yf<N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(A, B, tw, done);
+    k4_yf<T, N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(A, B, tw, done);
   }
   {
     LaunchScope ls(c, Site(s0 + 2));
-    k4_z<N1, N2><<<gy, kThreads, Gm::smem_z, c->stream>>>(B, c->M32, zero_dc, tw, done);
+    k4_z<T, N1, N2, TM><<<gy, kThreads, Gm::smem_z, c->stream>>>(B, M, zero_dc, tw, done);
   }
   {
     LaunchScope ls(c, Site(s0 + 3));
-    k4_yi<N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(B, A, tw, done);
+    k4_yi<T, N1, N2><<<gy, kThreads, Gm::smem_y, c->stream>>>(B, A, tw, done);
   }
   {
     LaunchScope ls(c, Site(s0 + 4));
-    k4_xi<N1, N2, Epi, Fin><<<gx, kThreads, Gm::smem_x, c->stream>>>(A, epi, fin, red_args(c),
-                                                                     tw, done);
+    k4_xi<T, N1, N2, Epi, Fin><<<gx, kThreads, Gm::smem_x, c->stream>>>(A, epi, fin, red_args(c),
+                                                                        tw, done);
   }
   check(cudaGetLastError(), "spectral pipeline launch");
+}
+
+// Dispatch on the context's four-step schedule (every entry of kFourStep,
+// ctx.h); false when the plan has none (Stockham stages).
+template <typename T, typename Pro, typename Epi, typename Fin>
+bool run_four_step(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0) {
+  switch (c->plan.f1 * 64 + c->plan.f2) {
+    case 16 * 64 + 16: run_pipeline4<T, 16, 16>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 16 * 64 + 12: run_pipeline4<T, 16, 12>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 12 * 64 + 16: run_pipeline4<T, 12, 16>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 16 * 64 + 8: run_pipeline4<T, 16, 8>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 8 * 64 + 16: run_pipeline4<T, 8, 16>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 12 * 64 + 8: run_pipeline4<T, 12, 8>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 8 * 64 + 12: run_pipeline4<T, 8, 12>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 8 * 64 + 8: run_pipeline4<T, 8, 8>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 8 * 64 + 4: run_pipeline4<T, 8, 4>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    default: return false;
+  }
 }
 
 // The five passes XF -> YF -> Z -> YI -> XI on the context's stream.
@@ -68,19 +107,7 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
   const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
                                 : (sizeof(T) == 8 ? S_XF64 : S_XF32);
   if constexpr (sizeof(T) == 4) {
-    switch (c->plan.f1 * 64 + c->plan.f2) {
-      // every entry of kFourStep (ctx.h)
-      case 16 * 64 + 16: return run_pipeline4<16, 16>(c, pro, epi, fin, zero_dc, done, s0);
-      case 16 * 64 + 12: return run_pipeline4<16, 12>(c, pro, epi, fin, zero_dc, done, s0);
-      case 12 * 64 + 16: return run_pipeline4<12, 16>(c, pro, epi, fin, zero_dc, done, s0);
-      case 16 * 64 + 8: return run_pipeline4<16, 8>(c, pro, epi, fin, zero_dc, done, s0);
-      case 8 * 64 + 16: return run_pipeline4<8, 16>(c, pro, epi, fin, zero_dc, done, s0);
-      case 12 * 64 + 8: return run_pipeline4<12, 8>(c, pro, epi, fin, zero_dc, done, s0);
-      case 8 * 64 + 12: return run_pipeline4<8, 12>(c, pro, epi, fin, zero_dc, done, s0);
-      case 8 * 64 + 8: return run_pipeline4<8, 8>(c, pro, epi, fin, zero_dc, done, s0);
-      case 8 * 64 + 4: return run_pipeline4<8, 4>(c, pro, epi, fin, zero_dc, done, s0);
-      default: break;
-    }
+    if (run_four_step<float>(c, pro, epi, fin, zero_dc, done, s0)) return;
   }
   const int n = c->n, h = n / 2 + 1;
   const size_t sm = G::smem_bytes(c->plan);
@@ -136,6 +163,14 @@ template <typename T> void grad_public(plc_ctx* c, const T* s, const T* w, const
 template <typename T, typename TS, typename TC>
 void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar, T* y,
                  T* g, TC* D, TC* r, bool jac) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<TC, float>::value) {
+    // the FP64 gradient of the mixed solve: float-float transforms where the
+    // length has a four-step schedule, FP64 epilogue
+    const EpiFF<EpiGrad<double, double, double, float>> epi{
+        EpiGrad<double, double, double, float>{s, w, N, nbar, c->mu, y, g, D, r, c->jac_c,
+                                               jac ? 1 : 0}};
+    if (run_four_step<ff>(c, ProShiftFF{s, c->mu}, epi, FinGrad{}, 0, nullptr, S_GXFF)) return;
+  }
   run_pipeline<T>(c, ProShift<T, TS>{s, c->mu},
                   EpiGrad<T, TS, double, TC>{s, w, N, nbar, c->mu, y, g, D, r, c->jac_c,
                                              jac ? 1 : 0},

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace plc {
 
@@ -108,7 +109,34 @@ template <typename T, bool JAC> struct ProCgDir {
   }
 };
 
+// s - mu formed in FP64 from an FP64 s and handed to float-float transforms
+// (the nearest float-float to the FP64 difference).
+struct ProShiftFF {
+  const double* s;
+  double mu;
+  __device__ void prepare() {}
+  __device__ void prefetch(size_t i, unsigned cnt) const { prefetch_l2(s + i, cnt * sizeof(double)); }
+  __device__ V4<ff> vec4(size_t i) const {
+    const V4<double> a = ld4(s + i);
+    return V4<ff>{{ff(a.v[0] - mu), ff(a.v[1] - mu), ff(a.v[2] - mu), ff(a.v[3] - mu)}};
+  }
+};
+
 // ------------------------------- epilogues --------------------------------
+// An FP64 epilogue behind float-float transforms: y = hi + lo in FP64.
+template <typename Epi> struct EpiFF {
+  static constexpr int NV = Epi::NV;
+  static constexpr unsigned MAXMASK = Epi::MAXMASK;
+  using Acc = typename Epi::Acc;
+  Epi epi;
+  __device__ void prefetch(size_t i, unsigned cnt) const { epi.prefetch(i, cnt); }
+  __device__ void vec4(size_t i, const V4<ff>& y, Acc* acc) const {
+    const V4<double> yd{{to_double(y.v[0]), to_double(y.v[1]), to_double(y.v[2]),
+                         to_double(y.v[3])}};
+    epi.vec4(i, yd, acc);
+  }
+};
+
 template <typename T> struct EpiStore {
   static constexpr int NV = 0;
   static constexpr unsigned MAXMASK = 0;

@@ -29,24 +29,31 @@
 // one warp, which hold the partner frequencies N - k of each other's k, so
 // the real-to-complex split and its inverse take a warp shuffle instead of
 // another trip through shared memory.  The prologue and epilogue see rows in
-// natural order through a staging buffer of real rows (pitch N + 8 floats),
-// so they keep their 16-byte vector accesses.
+// natural order through a staging buffer of real rows (pitch N + 8), so they
+// keep their 16-byte vector accesses.
+//
+// T is the arithmetic of the transforms: float (the FP32 operators and the
+// FP32 phase of the solve) or ff, float-float on the FP32 pipes (ff.cuh),
+// for the FP64 gradient of the mixed solve.
 #pragma once
 
+#include "ff.cuh"
+#include "ops.cuh"
 #include "passes.cuh"
 
 namespace plc {
 
-template <int N1_, int N2_> struct Geo4 {
+template <typename T, int N1_, int N2_> struct Geo4 {
+  using C = cpx<T>;
   static constexpr int N1 = N1_, N2 = N2_, N = N1 * N2;
   static constexpr int L = 16;            // lines per block
-  static constexpr int S = N + 1;         // pitch of the exchange buffer (float2)
+  static constexpr int S = N + 1;         // pitch of the exchange buffer (complex)
   static constexpr int RY = 2 * L;        // real rows per x-pass block
-  static constexpr int SR = N + 8;        // pitch of the real-row staging (floats)
-  static constexpr size_t tw_bytes = sizeof(float2) * N;
-  static constexpr size_t x_bytes = sizeof(float2) * L * S;
-  static constexpr size_t r_bytes = sizeof(float) * RY * SR;
-  static constexpr size_t m_bytes = sizeof(float) * L * (N / 2 + 1);   // Z multipliers
+  static constexpr int SR = N + 8;        // pitch of the real-row staging (reals)
+  static constexpr size_t tw_bytes = sizeof(C) * N;
+  static constexpr size_t x_bytes = sizeof(C) * L * S;
+  static constexpr size_t r_bytes = sizeof(T) * RY * SR;
+  static constexpr size_t m_bytes = sizeof(T) * L * (N / 2 + 1);   // Z multipliers
   static constexpr size_t smem_y = tw_bytes + x_bytes;
   static constexpr size_t smem_z = tw_bytes + x_bytes + m_bytes;
   static constexpr size_t smem_x = tw_bytes + (x_bytes > r_bytes ? x_bytes : r_bytes);
@@ -55,73 +62,74 @@ template <int N1_, int N2_> struct Geo4 {
 };
 
 // tw2[k1 N2 + n2] = W_N^{k1 n2} from the natural table tw[m] = W_N^m.
-template <int N1, int N2>
-__device__ __forceinline__ void load_tw2(float2* tw2, const float2* __restrict__ twg) {
+template <typename C, int N1, int N2>
+__device__ __forceinline__ void load_tw2(C* tw2, const C* __restrict__ twg) {
   for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) tw2[i] = twg[(i / N2) * (i % N2)];
 }
 
 // Phase A: DFT_N1 over n1 (sign SIGN), then twiddle by W_N^{SIGN-conjugated n2 k1}.
-template <int N1, int N2, int SIGN>
-__device__ __forceinline__ void phase_a(float2* v, const float2* tw2, int n2) {
-  dft_small<float, SIGN, N1>(v);
+template <typename T, int N1, int N2, int SIGN>
+__device__ __forceinline__ void phase_a(cpx<T>* v, const cpx<T>* tw2, int n2) {
+  dft_small<T, SIGN, N1>(v);
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) {
-    float2 w = tw2[k1 * N2 + n2];
+    cpx<T> w = tw2[k1 * N2 + n2];
     if (SIGN > 0) w.y = -w.y;
     v[k1] = cmul(v[k1], w);
   }
 }
 
 // Phase B': inverse DFT_N2 over k2, then the conjugate twiddle W_N^{-n2 k1}.
-template <int N1, int N2>
-__device__ __forceinline__ void phase_b_inv(float2* v, const float2* tw2, int k1) {
-  dft_small<float, +1, N2>(v);
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void phase_b_inv(cpx<T>* v, const cpx<T>* tw2, int k1) {
+  dft_small<T, +1, N2>(v);
 #pragma unroll
   for (int n2 = 1; n2 < N2; ++n2) {
-    float2 w = tw2[k1 * N2 + n2];
+    cpx<T> w = tw2[k1 * N2 + n2];
     w.y = -w.y;
     v[n2] = cmul(v[n2], w);
   }
 }
 
 #define PLC_PASS4_PROLOGUE(SMEM_TAIL)                                   \
-  using Gm = Geo4<N1, N2>;                                              \
+  using Gm = Geo4<T, N1, N2>;                                           \
+  using C = cpx<T>;                                                     \
   constexpr int N = Gm::N;                                              \
   if (done && *done) return;                                            \
   extern __shared__ __align__(16) unsigned char smem_raw[];             \
-  float2* tw2 = reinterpret_cast<float2*>(smem_raw);                    \
+  C* tw2 = reinterpret_cast<C*>(smem_raw);                              \
   SMEM_TAIL;                                                            \
-  load_tw2<N1, N2>(tw2, twg);                                           \
+  load_tw2<C, N1, N2>(tw2, twg);                                        \
   __syncthreads()
 
 // ---------------------------------------------------------------------------
 // YF: c2c along y.  grid = (n / 16, n/2+1); block (zb, kx) owns the lines
 // A[z0 + c][kx][:] and writes B[kx][:][z0 + c].
 // ---------------------------------------------------------------------------
-template <int N1, int N2>
+template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(kThreads)
-k4_yf(const float2* __restrict__ A, float2* __restrict__ B, const float2* __restrict__ twg,
+k4_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, const cpx<T>* __restrict__ twg,
       const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(float2* X = tw2 + N);
+  PLC_PASS4_PROLOGUE(C* X = tw2 + N);
   const int h = N / 2 + 1, z0 = blockIdx.x * Gm::L, kx = blockIdx.y;
   if (threadIdx.x < Gm::L * N2) {
     const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
-    const float2* src = A + ((size_t)(z0 + c) * h + kx) * N + n2;
-    float2 v[N1];
+    const C* src = A + ((size_t)(z0 + c) * h + kx) * N + n2;
+    C v[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[N2 * n1];
-    phase_a<N1, N2, -1>(v, tw2, n2);
+    phase_a<T, N1, N2, -1>(v, tw2, n2);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) X[c * Gm::S + k1 * N2 + n2] = v[k1];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
     const int c = t % Gm::L, k1 = t / Gm::L;
-    float2 v[N2];
+    C v[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) v[n2] = X[c * Gm::S + k1 * N2 + n2];
-    dft_small<float, -1, N2>(v);
-    float2* dst = B + ((size_t)kx * N + k1) * N + z0 + c;
+    dft_small<T, -1, N2>(v);
+    C* dst = B + ((size_t)kx * N + k1) * N + z0 + c;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) dst[(size_t)N1 * k2 * N] = v[k2];
   }
@@ -133,33 +141,32 @@ k4_yf(const float2* __restrict__ A, float2* __restrict__ B, const float2* __rest
 // The spectrum of each phase-B task stays in registers between the two
 // transforms.  zero_dc drops the DC mode.
 // ---------------------------------------------------------------------------
-template <int N1, int N2>
+template <typename T, int N1, int N2, typename TM>
 __global__ void __launch_bounds__(kThreads)
-k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
-     const float2* __restrict__ twg, const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(float2* X = tw2 + N;
-                     float* Ms = reinterpret_cast<float*>(X + Gm::L * Gm::S));
+k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
+     const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(C* X = tw2 + N; T* Ms = reinterpret_cast<T*>(X + Gm::L * Gm::S));
   const int ky0 = blockIdx.x * Gm::L, kx = blockIdx.y;
-  float2* line0 = B + ((size_t)kx * N + ky0) * N;
+  C* line0 = B + ((size_t)kx * N + ky0) * N;
   const bool task_a = threadIdx.x < Gm::L * N2;
   const int n2a = threadIdx.x % N2, ca = threadIdx.x / N2;
-  float2 v[N1 > N2 ? N1 : N2];
+  C v[N1 > N2 ? N1 : N2];
   if (task_a) {
-    const float2* src = line0 + (size_t)ca * N + n2a;
+    const C* src = line0 + (size_t)ca * N + n2a;
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[N2 * n1];
   }
   // while the lines load: the block's multipliers Ms[c][|mz|] =
   // M[kx^2 + my^2 + mz^2], gathered from the L2-resident table
   constexpr int HM = N / 2 + 1, MI = (Gm::L * HM + kThreads - 1) / kThreads;
-  float mv[MI];
+  T mv[MI];
 #pragma unroll
   for (int j = 0; j < MI; ++j) {
     const int i = threadIdx.x + j * kThreads;
     const int c = i / HM, mz = i - c * HM;
     const int ky = ky0 + c, my = min(ky, N - ky);
     const int m2 = kx * kx + my * my + mz * mz;
-    mv[j] = (i >= Gm::L * HM || (zero_dc && m2 == 0)) ? 0.f : __ldg(M + m2);
+    mv[j] = (i >= Gm::L * HM || (zero_dc && m2 == 0)) ? T(0.0) : T(__ldg(M + m2));
   }
 #pragma unroll
   for (int j = 0; j < MI; ++j) {
@@ -167,23 +174,23 @@ k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
     if (i < Gm::L * HM) Ms[i] = mv[j];
   }
   if (task_a) {
-    phase_a<N1, N2, -1>(v, tw2, n2a);
+    phase_a<T, N1, N2, -1>(v, tw2, n2a);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) X[ca * Gm::S + k1 * N2 + n2a] = v[k1];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
     const int c = t % Gm::L, k1 = t / Gm::L;
-    float2 u[N2];
+    C u[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) u[n2] = X[c * Gm::S + k1 * N2 + n2];
-    dft_small<float, -1, N2>(u);
+    dft_small<T, -1, N2>(u);
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       const int kz = k1 + N1 * k2, mz = min(kz, N - kz);
       u[k2] = cscale(u[k2], Ms[c * HM + mz]);
     }
-    phase_b_inv<N1, N2>(u, tw2, k1);
+    phase_b_inv<T, N1, N2>(u, tw2, k1);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = u[n2];
   }
@@ -191,8 +198,8 @@ k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
   if (task_a) {
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = X[ca * Gm::S + k1 * N2 + n2a];
-    dft_small<float, +1, N1>(v);
-    float2* dst = line0 + (size_t)ca * N + n2a;
+    dft_small<T, +1, N1>(v);
+    C* dst = line0 + (size_t)ca * N + n2a;
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) dst[N2 * n1] = v[n1];
   }
@@ -202,30 +209,30 @@ k4_z(float2* __restrict__ B, const float* __restrict__ M, int zero_dc,
 // YI: inverse c2c along y.  grid = (n / 16, n/2+1); block (zb, kx) reads
 // B[kx][:][z0 + c] and writes A[z0 + c][kx][:].
 // ---------------------------------------------------------------------------
-template <int N1, int N2>
+template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(kThreads)
-k4_yi(const float2* __restrict__ B, float2* __restrict__ A, const float2* __restrict__ twg,
+k4_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, const cpx<T>* __restrict__ twg,
       const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(float2* X = tw2 + N);
+  PLC_PASS4_PROLOGUE(C* X = tw2 + N);
   const int h = N / 2 + 1, z0 = blockIdx.x * Gm::L, kx = blockIdx.y;
   for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
     const int c = t % Gm::L, k1 = t / Gm::L;
-    const float2* src = B + ((size_t)kx * N + k1) * N + z0 + c;
-    float2 u[N2];
+    const C* src = B + ((size_t)kx * N + k1) * N + z0 + c;
+    C u[N2];
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) u[k2] = src[(size_t)N1 * k2 * N];
-    phase_b_inv<N1, N2>(u, tw2, k1);
+    phase_b_inv<T, N1, N2>(u, tw2, k1);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = u[n2];
   }
   __syncthreads();
   if (threadIdx.x < Gm::L * N2) {
     const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
-    float2 v[N1];
+    C v[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = X[c * Gm::S + k1 * N2 + n2];
-    dft_small<float, +1, N1>(v);
-    float2* dst = A + ((size_t)(z0 + c) * h + kx) * N + n2;
+    dft_small<T, +1, N1>(v);
+    C* dst = A + ((size_t)(z0 + c) * h + kx) * N + n2;
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) dst[N2 * n1] = v[n1];
   }
@@ -237,8 +244,37 @@ template <int N1> __device__ __forceinline__ int pair_k1(int g, int member) {
   return g == 0 ? (member ? N1 / 2 : 0) : (member ? N1 - g : g);
 }
 
-__device__ __forceinline__ float2 shfl_xor16(float2 a) {
-  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, 16), __shfl_xor_sync(0xffffffffu, a.y, 16));
+__device__ __forceinline__ float shfl_xor16(float a) { return __shfl_xor_sync(0xffffffffu, a, 16); }
+__device__ __forceinline__ ff shfl_xor16(ff a) { return ff(shfl_xor16(a.hi), shfl_xor16(a.lo)); }
+template <typename C> __device__ __forceinline__ C shfl_xor16(C a) {
+  return cmk<C>(shfl_xor16(a.x), shfl_xor16(a.y));
+}
+
+// Four consecutive reals of a staging row (16-byte aligned).
+__device__ __forceinline__ void st_row4(float* p, const V4<float>& u) {
+  *reinterpret_cast<float4*>(p) = make_float4(u.v[0], u.v[1], u.v[2], u.v[3]);
+}
+__device__ __forceinline__ void st_row4(ff* p, const V4<ff>& u) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(u.v[0].hi, u.v[0].lo, u.v[1].hi, u.v[1].lo);
+  reinterpret_cast<float4*>(p)[1] = make_float4(u.v[2].hi, u.v[2].lo, u.v[3].hi, u.v[3].lo);
+}
+__device__ __forceinline__ V4<float> ld_row4(const float* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{q.x, q.y, q.z, q.w}};
+}
+__device__ __forceinline__ V4<ff> ld_row4(const ff* p) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  return V4<ff>{{ff(a.x, a.y), ff(a.z, a.w), ff(b.x, b.y), ff(b.z, b.w)}};
+}
+
+// A pair of adjacent complex values (the spectra of the two packed rows).
+__device__ __forceinline__ void ld_pair(const ffc* p, ffc& a, ffc& b) {
+  a = p[0];
+  b = p[1];
+}
+__device__ __forceinline__ void st_pair(ffc* p, ffc a, ffc b) {
+  p[0] = a;
+  p[1] = b;
 }
 
 // ---------------------------------------------------------------------------
@@ -247,11 +283,11 @@ __device__ __forceinline__ float2 shfl_xor16(float2 a) {
 // Z = FFT(row_2c + i row_2c+1): X_a[k] = (Z[k] + conj Z[N-k]) / 2 and
 // X_b[k] = (Z[k] - conj Z[N-k]) / 2i, stored as a pair at A[z][k][y0+2c].
 // ---------------------------------------------------------------------------
-template <int N1, int N2, typename Pro>
+template <typename T, int N1, int N2, typename Pro>
 __global__ void __launch_bounds__(kThreads)
-k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
+k4_xf(Pro pro, cpx<T>* __restrict__ A, const cpx<T>* __restrict__ twg,
       const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(float* R = reinterpret_cast<float*>(tw2 + N); float2* X = tw2 + N);
+  PLC_PASS4_PROLOGUE(T* R = reinterpret_cast<T*>(tw2 + N); C* X = tw2 + N);
   pro.prepare();
   const int h = N / 2 + 1, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
   // prologue: 32 rows in natural order, four x per thread and step; the
@@ -260,7 +296,7 @@ k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
   const size_t row0 = ((size_t)z * N + y0) * N;
   if (threadIdx.x == 0) pro.prefetch(row0, Gm::RY * N);
   for (int base = threadIdx.x; base < TOT; base += B4 * kThreads) {
-    V4<float> u[B4];
+    V4<T> u[B4];
 #pragma unroll
     for (int q = 0; q < B4; ++q) {
       const int e = base + q * kThreads;
@@ -269,22 +305,20 @@ k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
 #pragma unroll
     for (int q = 0; q < B4; ++q) {
       const int e = base + q * kThreads;
-      if (e < TOT)
-        *reinterpret_cast<float4*>(&R[(e / Q) * Gm::SR + 4 * (e % Q)]) =
-            make_float4(u[q].v[0], u[q].v[1], u[q].v[2], u[q].v[3]);
+      if (e < TOT) st_row4(&R[(e / Q) * Gm::SR + 4 * (e % Q)], u[q]);
     }
   }
   __syncthreads();
   // phase A on (c, n2), n2 on consecutive lanes
   const bool task_a = threadIdx.x < Gm::L * N2;
   const int n2a = threadIdx.x % N2, ca = threadIdx.x / N2;
-  float2 v[N1 > N2 ? N1 : N2];
+  C v[N1 > N2 ? N1 : N2];
   if (task_a) {
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1)
-      v[n1] = make_float2(R[(2 * ca) * Gm::SR + N2 * n1 + n2a],
-                          R[(2 * ca + 1) * Gm::SR + N2 * n1 + n2a]);
-    phase_a<N1, N2, -1>(v, tw2, n2a);
+      v[n1] = cmk<C>(R[(2 * ca) * Gm::SR + N2 * n1 + n2a],
+                     R[(2 * ca + 1) * Gm::SR + N2 * n1 + n2a]);
+    phase_a<T, N1, N2, -1>(v, tw2, n2a);
   }
   __syncthreads();   // X overlays R
   if (task_a) {
@@ -299,17 +333,17 @@ k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
     const int k1 = pair_k1<N1>(g, member);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) v[n2] = X[c * Gm::S + k1 * N2 + n2];
-    dft_small<float, -1, N2>(v);
-    float2* dst = A + ((size_t)z * h + k1) * N + y0 + 2 * c;
-    auto put = [&](int k2, float2 zk, float2 zm) {   // zm = Z[N - k]
-      const float2 zc = cconj(zm);
-      const float2 s = cadd(zk, zc), d = csub(zk, zc);
-      st_pair(dst + (size_t)N1 * k2 * N, make_float2(0.5f * s.x, 0.5f * s.y),
-              make_float2(0.5f * d.y, -0.5f * d.x));
+    dft_small<T, -1, N2>(v);
+    C* dst = A + ((size_t)z * h + k1) * N + y0 + 2 * c;
+    auto put = [&](int k2, C zk, C zm) {   // zm = Z[N - k]
+      const C zc = cconj(zm);
+      const C s = cadd(zk, zc), d = csub(zk, zc);
+      st_pair(dst + (size_t)N1 * k2 * N, cmk<C>(halve(s.x), halve(s.y)),
+              cmk<C>(halve(d.y), -halve(d.x)));
     };
     if (g != 0) {
       // Z[N - (k1 + N1 k2)] is the partner's element N2 - 1 - k2
-      float2 pz[N2 / 2];
+      C pz[N2 / 2];
 #pragma unroll
       for (int j = 0; j < N2 / 2; ++j) pz[j] = shfl_xor16(v[N2 - 1 - j]);
 #pragma unroll
@@ -333,38 +367,38 @@ k4_xf(Pro pro, float2* __restrict__ A, const float2* __restrict__ twg,
 // (projection onto real fields).  The epilogue sees y = (S^-1 x)_i per cell
 // and accumulates Epi::NV sums; Fin runs once on the grid totals.
 // ---------------------------------------------------------------------------
-template <int N1, int N2, typename Epi, typename Fin>
+template <typename T, int N1, int N2, typename Epi, typename Fin>
 __global__ void __launch_bounds__(kThreads)
-k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
-      const float2* __restrict__ twg, const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(float* R = reinterpret_cast<float*>(tw2 + N); float2* X = tw2 + N);
+k4_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
+      const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
+  PLC_PASS4_PROLOGUE(T* R = reinterpret_cast<T*>(tw2 + N); C* X = tw2 + N);
   const int h = N / 2 + 1, nh = N / 2, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
   const size_t row0 = ((size_t)z * N + y0) * N;
   // the epilogue's operands do not depend on the transform: request them
   // into L2 now, so that their latency hides behind the transform
   if (threadIdx.x == 0) epi.prefetch(row0, Gm::RY * N);
   const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2 v[N1 > N2 ? N1 : N2];
+  C v[N1 > N2 ? N1 : N2];
   if (g < N1 / 2) {
     const int c = lane & 15, member = lane >> 4;
     const int k1 = pair_k1<N1>(g, member);
-    const float2* src = A + ((size_t)z * h + k1) * N + y0 + 2 * c;
+    const C* src = A + ((size_t)z * h + k1) * N + y0 + 2 * c;
     // own coefficients k = k1 + N1 k2 <= n/2: Z[k] and the partner form Zc
     constexpr int NL = N2 / 2 + 1;
-    float2 za[NL], zb[NL];
+    C za[NL], zb[NL];
     const int nload = (g == 0 && member == 0) ? N2 / 2 + 1 : N2 / 2;
 #pragma unroll
     for (int k2 = 0; k2 < NL; ++k2)
       if (k2 < nload) ld_pair(src + (size_t)N1 * k2 * N, za[k2], zb[k2]);
-    float2 zc[NL];
+    C zc[NL];
 #pragma unroll
     for (int k2 = 0; k2 < NL; ++k2) {
       if (k2 >= nload) continue;
-      float2 xa = za[k2], xb = zb[k2];
+      C xa = za[k2], xb = zb[k2];
       const int k = k1 + N1 * k2;
-      if (k == 0 || k == nh) { xa.y = 0.f; xb.y = 0.f; }
-      v[k2] = make_float2(xa.x - xb.y, xa.y + xb.x);
-      zc[k2] = make_float2(xa.x + xb.y, xb.x - xa.y);
+      if (k == 0 || k == nh) { xa.y = T(0.0); xb.y = T(0.0); }
+      v[k2] = cmk<C>(xa.x - xb.y, xa.y + xb.x);
+      zc[k2] = cmk<C>(xa.x + xb.y, xb.x - xa.y);
     }
     if (g != 0) {
       // Z[k1 + N1 k2] for k2 >= N2/2 is the partner's Zc at N2 - 1 - k2
@@ -377,7 +411,7 @@ k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
 #pragma unroll
       for (int k2 = N2 / 2; k2 < N2; ++k2) v[k2] = zc[N2 - 1 - k2];
     }
-    phase_b_inv<N1, N2>(v, tw2, k1);
+    phase_b_inv<T, N1, N2>(v, tw2, k1);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = v[n2];
   }
@@ -387,7 +421,7 @@ k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
   if (task_a) {
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = X[ca * Gm::S + k1 * N2 + n2a];
-    dft_small<float, +1, N1>(v);
+    dft_small<T, +1, N1>(v);
   }
   __syncthreads();   // R overlays X
   if (task_a) {
@@ -405,9 +439,7 @@ k4_xi(const float2* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
 #pragma unroll 2
   for (int e = threadIdx.x; e < TOT; e += kThreads) {
     const int row = e / Q, x = 4 * (e % Q);
-    const float4 q = *reinterpret_cast<const float4*>(&R[row * Gm::SR + x]);
-    const V4<float> y{{q.x, q.y, q.z, q.w}};
-    epi.vec4(row0 + (size_t)row * N + x, y, acc);
+    epi.vec4(row0 + (size_t)row * N + x, ld_row4(&R[row * Gm::SR + x]), acc);
   }
   if constexpr (Epi::NV > 0) {
     double tot[Epi::NV];

@@ -146,3 +146,17 @@ def test_map_mixed_vs_fp64_selection128(plc):
     s32, _ = _gpu_map(plc, m, "mixed", 1e-6)
     assert np.max(np.abs(s32 - s64)) <= 1e-4
     assert rel_l2(s32, s64) <= 1e-5
+
+
+@pytest.mark.parametrize("key", ["plain32", "sel48"])
+def test_map_mixed_to_fp64_accuracy(plc, key):
+    """The mixed form driven to ||g|| / ||g0|| < 1e-10: past the switch the
+    state, gradient and stop test are FP64 (the refresh gradient through
+    float-float transforms at 32^3, FP64 Stockham at 48^3) while the CG stays
+    FP32, so the iteration refines to the FP64 MAP (per-voxel 1e-8)."""
+    m = _mock(key)
+    _, ref = _oracle_map(key, m)
+    s, st = _gpu_map(plc, m, "mixed", 1e-10)
+    assert st["grad_rel"] < 1e-10 and st["grad_ffts_fp64"] >= 1
+    err = np.abs(s - ref.s) / np.maximum(np.abs(ref.s), 1.0)
+    assert err.max() <= 1e-8
