@@ -86,8 +86,8 @@ template <typename T> void dalloc(T** p, size_t bytes) {
 void release(plc_ctx* c) {
   plc::graph_release(c);
   plc::profile_release(c);
-  void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->twff, c->M64, c->M32, c->lk, c->lP,
-                  c->sc, c->partials};
+  void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->twff, c->expff, c->M64, c->M32,
+                  c->lk, c->lP, c->sc, c->partials};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->wf)
@@ -214,6 +214,7 @@ plc_status plc_create(plc_ctx** out, int n, double box, int precision, void* str
     dalloc(&c->tw64, sizeof(double2) * n);
     dalloc(&c->tw32, sizeof(float2) * n);
     dalloc(&c->twff, sizeof(float4) * n);
+    dalloc(&c->expff, sizeof(float2) * 64);
     dalloc(&c->sc, sizeof(plc::DevScalars));
     plc::check(cudaMallocHost(reinterpret_cast<void**>(&c->sc_host), sizeof(plc::DevScalars)),
                "cudaMallocHost");
@@ -234,6 +235,13 @@ plc_status plc_create(plc_ctx** out, int n, double box, int precision, void* str
     plc::check(cudaMemcpyAsync(c->tw64, t64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
     plc::check(cudaMemcpyAsync(c->tw32, t32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
     plc::check(cudaMemcpyAsync(c->twff, tff.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->stream), "copy twiddles");
+    // 2^(j/64), j < 64, in float-float (the table of the float-float exp)
+    std::vector<float2> e2(64);
+    for (int j = 0; j < 64; ++j) {
+      const double v = std::exp2((double)j / 64.0);
+      e2[j] = make_float2((float)v, (float)(v - (double)(float)v));
+    }
+    plc::check(cudaMemcpyAsync(c->expff, e2.data(), sizeof(float2) * 64, cudaMemcpyHostToDevice, c->stream), "copy exp table");
     plc::check(cudaMemsetAsync(c->sc, 0, sizeof(plc::DevScalars), c->stream), "clear scalars");
     plc::check(cudaStreamSynchronize(c->stream), "stream synchronize");
     return PLC_OK;

@@ -65,6 +65,7 @@ struct plc_ctx {
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   void* twff = nullptr;        // float-float twiddles (ffc, ff.cuh)
+  void* expff = nullptr;       // 2^(j/64), j < 64, float-float (exp_ff)
 
   // Prior: inverse eigenvalue per |m|^2, its FP32 copy, ln-tables.
   double* M64 = nullptr;

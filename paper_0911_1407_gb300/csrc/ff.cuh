@@ -63,5 +63,43 @@ __device__ __forceinline__ ff halve(ff a) { return ff(0.5f * a.hi, 0.5f * a.lo);
 
 __device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ ff ff_abs(ff a) { return a.hi < 0.f ? -a : a; }
+
+// exp(x) of an FP64 argument in float-float, by the table-driven method of
+// Tang (ACM TOMS 15, 1989) with 64 table points: x = (64 m + j) ln2/64 + r,
+// |r| <= ln2/128, exp(x) = 2^m 2^(j/64) (1 + p(r)), p the Taylor polynomial
+// of exp(r) - 1 to degree 5 (remainder below 4e-17).  The reduction is done
+// in float-float, so the relative error is a few 2^-48 of max(|x|, 1).
+// tab[j] = 2^(j/64) in float-float (device memory, read through L1).
+// For |x| < 80.
+__device__ __forceinline__ ff exp_ff(double x, const ff* __restrict__ tab) {
+  const ff xf(x);
+  const float nf = rintf(xf.hi * 92.332482616893657f);     // 64 / ln 2
+  const int nn = (int)nf;
+  const int j = nn & 63, m = (nn - j) / 64;
+  // ln2 / 64 as a float-float; nf is an integer below 2^13, exact in float
+  const ff l64(1.083042473e-02f, -2.976022206e-11f);
+  const ff r = xf - ff(nf, 0.f) * l64;
+  // p(r) = r + r^2 (1/2 + r (1/6 + r (1/24 + r / 120))): the inner part to
+  // float accuracy suffices (it carries r^3 / 6 < 3e-8)
+  const float q = fmaf(fmaf(r.hi, 1.f / 120.f, 1.f / 24.f), r.hi, 1.f / 6.f);
+  const float rq = r.hi * q;
+  const float t_hi = 0.5f + rq;
+  const ff t(t_hi, rq - (t_hi - 0.5f));                    // Fast2Sum, |rq| < 0.5
+  const ff p = r + (r * r) * t;
+  const float2 tj = __ldg(reinterpret_cast<const float2*>(tab) + j);
+  const ff sj(tj.x, tj.y);
+  const ff e = sj + sj * p;
+  return ff(ldexpf(e.hi, m), ldexpf(e.lo, m));
+}
+
+// Sum accumulator in float-float (for sums that must carry FP64-level
+// accuracy out of float-float arithmetic).
+struct AccFF {
+  ff s;
+  __device__ void init(bool) { s = ff(0.f, 0.f); }
+  __device__ void add(ff x) { s = s + x; }
+  __device__ double get() const { return to_double(s); }
+};
 
 }  // namespace plc

@@ -123,6 +123,66 @@ struct ProShiftFF {
 };
 
 // ------------------------------- epilogues --------------------------------
+// The gradient epilogue of EpiGrad for float-float transforms (the FP64
+// gradient of the mixed solve), kept in float-float so that it needs no FP64
+// arithmetic beyond format conversions: y (from the transform), s (FP64 in
+// memory), D = nbar w e^s (exp_ff), g = y + D - N and the six sums of
+// EpiGrad are float-float; y and g are stored in FP64, D and r = -g in FP32.
+struct EpiGradFF {
+  static constexpr int NV = 6;
+  static constexpr unsigned MAXMASK = 0;
+  using Acc = AccFF;
+  const double* s;
+  const double* w;      // may be null
+  const int32_t* N;
+  double nbar, mu;
+  double* yout;
+  double* g;
+  float* D;
+  float* r;
+  float c;              // Jacobi constant (S^-1)_ii
+  int jac;
+  const ff* exptab;     // 2^(j/64), j < 64
+  __device__ void prefetch(size_t i, unsigned cnt) const {
+    prefetch_l2(s + i, cnt * sizeof(double));
+    prefetch_l2(N + i, cnt * sizeof(int32_t));
+    if (w) prefetch_l2(w + i, cnt * sizeof(double));
+  }
+  __device__ void vec4(size_t i, const V4<ff>& y, Acc* acc) const {
+    const V4<double> sv = ld4(s + i);
+    const V4<int32_t> nv = ld4(N + i);
+    V4<double> wv{{1.0, 1.0, 1.0, 1.0}};
+    if (w) wv = ld4(w + i);
+    const ff nb(nbar), m(mu);
+    V4<double> yo, go;
+    V4<float> dv, rv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const ff st(sv.v[j]);
+      ff d = nb * exp_ff(sv.v[j], exptab);
+      if (w) d = d * ff(wv.v[j]);
+      const ff ni((float)nv.v[j], 0.f);    // counts below 2^24 are exact
+      const ff gi = (y.v[j] + d) - ni;
+      const ff ns = ni * st;
+      acc[0].add((st - m) * y.v[j]);
+      acc[1].add(d - ns);
+      acc[2].add(gi * gi);
+      acc[3].add(ns);
+      acc[4].add(ni * ff_abs(st));
+      const float gc = gi.hi + gi.lo, dc = d.hi + d.lo;
+      acc[5].add(ff(jac ? gc * jacobi(gc, dc, c) : gc * gc, 0.f));
+      yo.v[j] = to_double(y.v[j]);
+      go.v[j] = to_double(gi);
+      dv.v[j] = dc;
+      rv.v[j] = -gc;
+    }
+    if (yout) st4(yout + i, yo);
+    if (g) st4(g + i, go);
+    if (D) st4(D + i, dv);
+    if (r) st4(r + i, rv);
+  }
+};
+
 // An FP64 epilogue behind float-float transforms: y = hi + lo in FP64.
 template <typename Epi> struct EpiFF {
   static constexpr int NV = Epi::NV;
