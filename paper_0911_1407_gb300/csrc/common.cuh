@@ -305,13 +305,25 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // arithmetic per element, which runs at a small fraction of the FP32 rate).
 // Across threads and blocks the sums continue in FP64.
 // ---------------------------------------------------------------------------
+// Per-thread accumulators.  Besides add/max, each can merge another one of
+// its kind (merge) and move across lanes (shfl_down), so that a block
+// reduces them in their own arithmetic: GB300's FP64 rate is 1/64 of FP32,
+// and FP64 adds in the warp reductions of FP32 kernels cost several
+// microseconds per launch.
 struct AccD {
   double v;
   __device__ __forceinline__ void init(bool is_max) { v = is_max ? -INFINITY : 0.0; }
   __device__ __forceinline__ void add(double x) { v += x; }
   __device__ __forceinline__ void max(double x) { v = fmax(v, x); }
   __device__ __forceinline__ double get() const { return v; }
+  __device__ __forceinline__ void merge(const AccD& o, bool is_max) {
+    v = is_max ? fmax(v, o.v) : v + o.v;
+  }
+  __device__ __forceinline__ AccD shfl_down(int o) const {
+    return AccD{__shfl_down_sync(0xffffffffu, v, o)};
+  }
 };
+// Kahan-compensated FP32 sum: value s - c.
 struct AccK {
   float s, c;
   __device__ __forceinline__ void init(bool is_max) { s = is_max ? -INFINITY : 0.f; c = 0.f; }
@@ -323,6 +335,22 @@ struct AccK {
   }
   __device__ __forceinline__ void max(float x) { s = fmaxf(s, x); }
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+  // (s1 - c1) + (s2 - c2): the high parts by TwoSum (Knuth), the rounding
+  // error folded into the compensation
+  __device__ __forceinline__ void merge(const AccK& o, bool is_max) {
+    if (is_max) {
+      s = fmaxf(s, o.s);
+      return;
+    }
+    const float t = s + o.s;
+    const float bb = t - s;
+    const float e = (s - (t - bb)) + (o.s - bb);
+    c = (c + o.c) - e;
+    s = t;
+  }
+  __device__ __forceinline__ AccK shfl_down(int o) const {
+    return AccK{__shfl_down_sync(0xffffffffu, s, o), __shfl_down_sync(0xffffffffu, c, o)};
+  }
 };
 template <typename T> struct AccOf;
 template <> struct AccOf<double> { using type = AccD; };
@@ -376,13 +404,13 @@ __device__ __forceinline__ void block_reduce(double* v, double* sh) {
   __syncthreads();
 }
 
+// The grid reduction behind block_reduce_finish: v (thread 0's block
+// totals) to the partials; the last block sums them in block order.
 template <int NV, unsigned MAXMASK, typename Fin>
-__device__ __forceinline__ void block_reduce_finish(double* v, const RedArgs& ra, Fin fin) {
-  __shared__ double sh[32 * kMaxRed];
+__device__ __forceinline__ void grid_finish(double* v, const RedArgs& ra, Fin fin, double* sh) {
   __shared__ int is_last;
   const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
   const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_reduce<NV, MAXMASK>(v, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) ra.partials[(size_t)bid * kMaxRed + j] = v[j];
@@ -407,6 +435,49 @@ __device__ __forceinline__ void block_reduce_finish(double* v, const RedArgs& ra
     ra.sc->ticket = 0u;
     __threadfence();
   }
+}
+
+// Deterministic grid reduction of per-thread FP64 values v[NV].
+template <int NV, unsigned MAXMASK, typename Fin>
+__device__ __forceinline__ void block_reduce_finish(double* v, const RedArgs& ra, Fin fin) {
+  __shared__ double sh[32 * kMaxRed];
+  block_reduce<NV, MAXMASK>(v, sh);
+  grid_finish<NV, MAXMASK>(v, ra, fin, sh);
+}
+
+// The same from per-thread accumulators: lanes and warps are merged in the
+// accumulators' own arithmetic in a fixed order, and each block's totals
+// go to FP64 once.
+template <int NV, unsigned MAXMASK, typename Acc, typename Fin>
+__device__ __forceinline__ void block_reduce_finish_acc(Acc* a, const RedArgs& ra, Fin fin) {
+  __shared__ Acc sa[32 * kMaxRed];
+  __shared__ double sh[32 * kMaxRed];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) a[j].merge(a[j].shfl_down(o), (MAXMASK >> j) & 1u);
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sa[warp * NV + j] = a[j];
+  __syncthreads();
+  double v[NV];
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (lane < nw) a[j] = sa[lane * NV + j];
+      else a[j].init((MAXMASK >> j) & 1u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) a[j].merge(a[j].shfl_down(o), (MAXMASK >> j) & 1u);
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = a[j].get();
+  __syncthreads();
+  grid_finish<NV, MAXMASK>(v, ra, fin, sh);
 }
 
 // Grid size for element-wise kernels: a fixed multiple of the SM count so

@@ -100,6 +100,10 @@ struct AccFF {
   __device__ void init(bool) { s = ff(0.f, 0.f); }
   __device__ void add(ff x) { s = s + x; }
   __device__ double get() const { return to_double(s); }
+  __device__ void merge(const AccFF& o, bool) { s = s + o.s; }
+  __device__ AccFF shfl_down(int o) const {
+    return AccFF{ff(__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o))};
+  }
 };
 
 }  // namespace plc

@@ -421,7 +421,7 @@ k_cg_init(const TB* __restrict__ b, const TC* __restrict__ D, TC c, TC* __restri
     a0.add(ri * zi);
     a1.add(ri * ri);
   }
-  double acc[2] = {a0.get(), a1.get()};
+  typename AccOf<TC>::type acc[2] = {a0, a1};
   struct Fin {
     __device__ void operator()(const double* t, DevScalars* sc) const {
       sc->rz = t[0];
@@ -437,7 +437,7 @@ k_cg_init(const TB* __restrict__ b, const TC* __restrict__ D, TC c, TC* __restri
       sc->done = t[1] <= 0.0 ? 1 : 0;
     }
   };
-  block_reduce_finish<2, 0u>(acc, ra, Fin{});
+  block_reduce_finish_acc<2, 0u>(acc, ra, Fin{});
 }
 
 // x += alpha p (x = alpha p on the first step, so x needs no clearing),
@@ -475,7 +475,7 @@ k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
     st4(x + i, xv);
     st4(r + i, rv);
   }
-  double acc[3] = {a0.get(), a1.get(), a2.get()};
+  typename AccOf<TC>::type acc[3] = {a0, a1, a2};
   struct Fin {
     double rtol2;
     int max_iter;
@@ -490,7 +490,7 @@ k_cg_update(TC* __restrict__ x, TC* __restrict__ r, const TC* __restrict__ p,
       if (t[1] <= rt2 * sc->bnorm2 || sc->iter >= mi) sc->done = 1;
     }
   };
-  block_reduce_finish<3, 1u << 2>(acc, ra, Fin{rtol2, max_iter});
+  block_reduce_finish_acc<3, 1u << 2>(acc, ra, Fin{rtol2, max_iter});
 }
 
 // A Newton trial point without an FFT.  S^-1 is linear, so with the CG's
@@ -555,10 +555,7 @@ k_newton_update(const T* __restrict__ s, const T* __restrict__ y, const T* __res
     st4(D2 + i, dout);
     st4(r2 + i, rout);
   }
-  double tot[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) tot[j] = acc[j].get();
-  block_reduce_finish<6, 0u>(tot, ra, FinGrad{});
+  block_reduce_finish_acc<6, 0u>(acc, ra, FinGrad{});
 }
 
 // D = nbar w e^s (Sec. 3.1.2), from an FP64 s.

@@ -327,12 +327,7 @@ k_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra, FftPlan plan,
     }
     epi.vec4(((size_t)z * n + (y0 + row)) * n + x, y, acc);
   }
-  if constexpr (Epi::NV > 0) {
-    double tot[Epi::NV];
-#pragma unroll
-    for (int j = 0; j < Epi::NV; ++j) tot[j] = acc[j].get();
-    block_reduce_finish<Epi::NV, Epi::MAXMASK>(tot, ra, fin);
-  }
+  if constexpr (Epi::NV > 0) block_reduce_finish_acc<Epi::NV, Epi::MAXMASK>(acc, ra, fin);
 }
 
 #undef PLC_PASS_PROLOGUE

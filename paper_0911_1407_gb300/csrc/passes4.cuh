@@ -53,7 +53,12 @@ template <typename T, int N1_, int N2_> struct Geo4 {
   static constexpr size_t tw_bytes = sizeof(C) * N;
   static constexpr size_t x_bytes = sizeof(C) * L * S;
   static constexpr size_t r_bytes = sizeof(T) * RY * SR;
-  static constexpr size_t m_bytes = sizeof(T) * L * (N / 2 + 1);   // Z multipliers
+  // Z multipliers Ms[c][|mz|], |mz| <= N/2: pitch N/2 + 1 (odd) for 8-byte
+  // reals, N/2 + 2 (twice an odd number for N a multiple of 8) for floats, so
+  // that the lines c of both half-warps of a phase-B warp (which differ by
+  // one in |mz|) fall in distinct banks
+  static constexpr int MP = sizeof(T) == 4 ? N / 2 + 2 : N / 2 + 1;
+  static constexpr size_t m_bytes = sizeof(T) * L * MP;
   static constexpr size_t smem_y = tw_bytes + x_bytes;
   static constexpr size_t smem_z = tw_bytes + x_bytes + m_bytes;
   static constexpr size_t smem_x = tw_bytes + (x_bytes > r_bytes ? x_bytes : r_bytes);
@@ -158,7 +163,7 @@ k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
   }
   // while the lines load: the block's multipliers Ms[c][|mz|] =
   // M[kx^2 + my^2 + mz^2], gathered from the L2-resident table
-  constexpr int HM = N / 2 + 1, MI = (Gm::L * HM + kThreads - 1) / kThreads;
+  constexpr int HM = N / 2 + 1, MI = (Gm::L * HM + kThreads - 1) / kThreads, MP = Gm::MP;
   T mv[MI];
 #pragma unroll
   for (int j = 0; j < MI; ++j) {
@@ -171,7 +176,7 @@ k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
 #pragma unroll
   for (int j = 0; j < MI; ++j) {
     const int i = threadIdx.x + j * kThreads;
-    if (i < Gm::L * HM) Ms[i] = mv[j];
+    if (i < Gm::L * HM) Ms[(i / HM) * MP + i % HM] = mv[j];
   }
   if (task_a) {
     phase_a<T, N1, N2, -1>(v, tw2, n2a);
@@ -188,7 +193,7 @@ k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       const int kz = k1 + N1 * k2, mz = min(kz, N - kz);
-      u[k2] = cscale(u[k2], Ms[c * HM + mz]);
+      u[k2] = cscale(u[k2], Ms[c * MP + mz]);
     }
     phase_b_inv<T, N1, N2>(u, tw2, k1);
 #pragma unroll
@@ -441,12 +446,7 @@ k4_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
     const int row = e / Q, x = 4 * (e % Q);
     epi.vec4(row0 + (size_t)row * N + x, ld_row4(&R[row * Gm::SR + x]), acc);
   }
-  if constexpr (Epi::NV > 0) {
-    double tot[Epi::NV];
-#pragma unroll
-    for (int j = 0; j < Epi::NV; ++j) tot[j] = acc[j].get();
-    block_reduce_finish<Epi::NV, Epi::MAXMASK>(tot, ra, fin);
-  }
+  if constexpr (Epi::NV > 0) block_reduce_finish_acc<Epi::NV, Epi::MAXMASK>(acc, ra, fin);
 }
 
 #undef PLC_PASS4_PROLOGUE
