@@ -530,6 +530,20 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
         e1.record(stream)
         torch.cuda.synchronize()
     line["host_driven_ms"] = e0.elapsed_time(e1)
+    # the LSQ-Wiener filter on the same data (one CG solve of
+    # (S^-1 + diag(nbar w)) delta = N - nbar w)
+    lsq = {}
+    for prec, cc, tol in (("mixed", ctx, 1e-6), ("fp64", ctx64, 1e-6)):
+        d = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+        cc.wiener_lsq(N_dev, None, m.nbar, out=d, tol=tol)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, _, st = cc.wiener_lsq(N_dev, None, m.nbar, out=d, tol=tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lsq[prec] = {"ms": e0.elapsed_time(e1), "cg_iters": st["cg_iters"],
+                     "rel_residual": st["grad_rel"]}
+    line["lsq_wiener"] = lsq
     batch_extra(plc, line)
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:

@@ -153,6 +153,38 @@ plc_status plc_newton_krylov_map(plc_ctx* ctx, const int32_t* N, const void* w,
                                  double nbar, double* s_inout,
                                  const plc_opts* opts, plc_stats* stats);
 
+/* MAP of the Gaussian-prior Poisson model with unity bias (Sec. 2.2.2,
+ * Eq. MAPG; gradient and Hessian of Sec. 3.1.1 without the factor S): the
+ * overdensity delta minimising
+ *   1/2 delta^T S^-1 delta + sum_i [ nbar w_i (1 + delta_i) - N_i ln(1 + delta_i) ]
+ * over 1 + delta_i > 0 where N_i > 0 (cells with N_i = 0 may go below -1).
+ * The same inexact Newton-Krylov iteration and precision scheme as
+ * plc_newton_krylov_map (host-driven; opts->device_driven is not used), with
+ * the step kept inside the domain by the fraction to the boundary,
+ * tau <= 0.99 / max(-xi_i / (1 + delta_i)) over cells with N_i > 0, instead
+ * of opts->step_cap.  S is the context's prior (mu is not used: the prior
+ * of delta has mean 0).  delta_inout (double, device): start point on entry
+ * (0 = the prior mean; it must satisfy 1 + delta > 0 where N > 0), MAP on
+ * exit.  N: int32 field; w: double field or NULL.  Synchronises the stream. */
+plc_status plc_gauss_map(plc_ctx* ctx, const int32_t* N, const void* w, double nbar,
+                         double* delta_inout, const plc_opts* opts, plc_stats* stats);
+
+/* LSQ-Wiener filter with unity bias (Sec. 4.1.1, Eq. WF; Table 1, Gaussian
+ * prior and Gaussian likelihood): the linear estimate of the overdensity
+ *   delta = (S^-1 + diag(nbar w))^-1 (N - nbar w),
+ * from the data vector N / nbar - w (Eq. datamodel) with noise covariance
+ * diag(w / nbar) (Eq. noiseav).  S is the context's prior (its mean mu is
+ * not used: the prior of delta has mean 0).  Solved by Jacobi-preconditioned
+ * CG from delta = 0 to relative residual opts->tol (the CG runs in FP32 for
+ * a PLC_MIXED context, so about 1e-6 at best), on the context's stream; the
+ * other options are not used.  N: int32 field; w: double field or NULL;
+ * delta_out: double field.  stats: cg_iters, hv_count, grad_rel (the final
+ * relative residual), g0_norm (||N - nbar w||), ms.  Returns
+ * PLC_ERR_NOT_CONVERGED (delta_out holding the last iterate) when max_cg is
+ * reached.  Synchronises the stream. */
+plc_status plc_wiener_lsq(plc_ctx* ctx, const int32_t* N, const void* w, double nbar,
+                          double* delta_out, const plc_opts* opts, plc_stats* stats);
+
 /* Implicit adjoint of the MAP (implicit-function theorem on g(s*) = 0; the
  * paper has no counterpart).  For a cotangent u (double field), solves
  * H lam = u by CG at s_map and returns

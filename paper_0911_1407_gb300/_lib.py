@@ -25,7 +25,7 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
-           "plc_set_fft_schedule", "plc_autotune",
+           "plc_gauss_map", "plc_wiener_lsq", "plc_set_fft_schedule", "plc_autotune",
            "plc_batch_create", "plc_batch_map", "plc_batch_destroy",
            "plc_profile_enable", "plc_profile_read", "plc_hessvec_noalloc", "plc_last_error",
            "plc_status_string"]
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_default_opts": (I, [ctypes.POINTER(Opts)]),
         "plc_newton_krylov_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_wiener_lsq": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_gauss_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_set_fft_schedule": (I, [P, I, I]),
         "plc_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), DP]),
         "plc_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I]),
@@ -247,6 +249,34 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return MapResult(s, st, stt.as_dict())
+
+    def gauss_map(self, N, w, nbar: float, delta: Optional[torch.Tensor] = None,
+                  raise_on_fail: bool = True, **opts) -> MapResult:
+        """MAP of the Gaussian-prior Poisson model; delta (float64) is the
+        start point (default 0) and is overwritten."""
+        if delta is None:
+            delta = torch.zeros((self.n,) * 3, dtype=torch.float64, device="cuda")
+        o, stt = default_opts(**opts), Stats()
+        st = self.lib.plc_gauss_map(
+            self._h, _ptr(N, self.n, torch.int32, "N"), _ptr(w, self.n, torch.float64, "w", False),
+            float(nbar), _ptr(delta, self.n, torch.float64, "delta"), ctypes.byref(o),
+            ctypes.byref(stt))
+        if raise_on_fail:
+            self._check(st)
+        return MapResult(delta, st, stt.as_dict())
+
+    def wiener_lsq(self, N, w, nbar: float, out: Optional[torch.Tensor] = None,
+                   raise_on_fail: bool = True, **opts):
+        """LSQ-Wiener estimate of delta (float64 field); returns (delta, status, stats)."""
+        out = self.field(torch.float64) if out is None else out
+        o, stt = default_opts(**opts), Stats()
+        st = self.lib.plc_wiener_lsq(
+            self._h, _ptr(N, self.n, torch.int32, "N"), _ptr(w, self.n, torch.float64, "w", False),
+            float(nbar), _ptr(out, self.n, torch.float64, "delta_out"), ctypes.byref(o),
+            ctypes.byref(stt))
+        if raise_on_fail:
+            self._check(st)
+        return out, st, stt.as_dict()
 
     def set_fft_schedule(self, f1: int, f2: int):
         """FP32 line-transform schedule: four-step n = f1 f2, or (0, 0) Stockham."""

@@ -403,6 +403,51 @@ plc_status plc_newton_krylov_map(plc_ctx* c, const int32_t* N, const void* w, do
   });
 }
 
+plc_status plc_gauss_map(plc_ctx* c, const int32_t* N, const void* w, double nbar,
+                         double* delta_inout, const plc_opts* opts, plc_stats* stats) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, delta_inout, "delta_inout", true));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  const plc_opts o = resolve_opts(opts);
+  PLC_TRY(check_opts(c, o));
+  return guarded(c, [&]() -> plc_status {
+    ensure_work_fields(c);
+    const double* wd = static_cast<const double*>(w);
+    const plc_status st = c->precision == PLC_FP64
+                              ? plc::gauss_map<double>(c, N, wd, nbar, delta_inout, o, stats)
+                              : plc::gauss_map<float>(c, N, wd, nbar, delta_inout, o, stats);
+    if (st == PLC_ERR_NOT_CONVERGED) fail(c, st, "Newton iteration cap reached");
+    else if (st == PLC_ERR_NONFINITE) fail(c, st, "non-finite gradient or objective");
+    else if (st == PLC_ERR_CG_BREAKDOWN) fail(c, st, "CG breakdown on the first step");
+    else c->err.clear();
+    return st;
+  });
+}
+
+plc_status plc_wiener_lsq(plc_ctx* c, const int32_t* N, const void* w, double nbar,
+                          double* delta_out, const plc_opts* opts, plc_stats* stats) {
+  PLC_TRY(need_prior(c));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, delta_out, "delta_out", true));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  const plc_opts o = resolve_opts(opts);
+  PLC_TRY(check_opts(c, o));
+  return guarded(c, [&]() -> plc_status {
+    ensure_work_fields(c);
+    const double* wd = static_cast<const double*>(w);
+    const plc_status st = c->precision == PLC_FP64
+                              ? plc::wiener_lsq<double>(c, N, wd, nbar, delta_out, o, stats)
+                              : plc::wiener_lsq<float>(c, N, wd, nbar, delta_out, o, stats);
+    if (st == PLC_ERR_NOT_CONVERGED) fail(c, st, "CG did not reach the tolerance");
+    else if (st == PLC_ERR_CG_BREAKDOWN) fail(c, st, "CG breakdown on the first step");
+    else c->err.clear();
+    return st;
+  });
+}
+
 plc_status plc_map_vjp(plc_ctx* c, const double* s_map, const void* w, double nbar,
                        const double* u, double* vjp_N, double* vjp_lnA, const plc_opts* opts,
                        plc_stats* stats) {

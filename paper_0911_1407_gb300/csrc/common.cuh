@@ -71,6 +71,8 @@ struct DevScalars {
   int max_iter;
   // step length of the next Newton trial (device-driven solve)
   double tau;
+  // fraction-to-boundary quantity of the Gaussian-prior model (k_boundary)
+  double bmax;
 };
 
 template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {

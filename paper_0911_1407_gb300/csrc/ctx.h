@@ -24,7 +24,7 @@ enum Site {
   // the FP64 gradient of the mixed solve in float-float transforms
   S_GXFF, S_GYFF, S_GZFF, S_GYIFF, S_GXIFF,
   S_CG_INIT, S_CG_UPDATE64, S_CG_UPDATE32, S_NEWTON_UPDATE64, S_NEWTON_UPDATE32,
-  S_DIAG, S_CONVERT, S_SETUP,
+  S_DIAG, S_CONVERT, S_SETUP, S_BOUNDARY,
   S_NSITES
 };
 extern const char* const kSiteNames[S_NSITES];
@@ -127,10 +127,24 @@ void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, 
                    bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2,
                    const double* tau_dev = nullptr);   // non-null: tau read on the device
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac);
+// The Gaussian-prior model (Eq. MAPG): gradient through the FFT at delta,
+// line-search trial, and the fraction-to-boundary quantity (into sc->bmax).
+template <typename T, typename TS, typename TC>
+void grad_newton_g(plc_ctx* c, const TS* delta, const double* w, const int32_t* N, double nbar,
+                   T* y, T* g, TC* D, TC* r, bool jac);
+template <typename T, typename TC>
+void newton_update_g(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
+                     const TC* D, const int32_t* N, const double* w, double nbar, double tau,
+                     bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2);
+template <typename T, typename TC>
+void boundary_step(plc_ctx* c, const T* delta, const TC* xi, const int32_t* N);
 template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL* lam);
 
 // Element-wise kernels.
 template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC* r, bool jac);
+// LSQ-Wiener filter start: D = nbar w, r = N - nbar w, CG scalars.
+template <typename TC> void lsq_init(plc_ctx* c, const int32_t* N, const double* w, double nbar,
+                                     TC* D, TC* r, bool jac);
 // rtol2 < 0: the stopping parameters are read from the device scalars.
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,
                                       const TC* D, bool jac, double rtol2, int max_iter);

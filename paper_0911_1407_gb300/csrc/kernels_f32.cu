@@ -15,8 +15,18 @@ template void newton_update<float, float>(plc_ctx*, const float*, const float*, 
                                           const float*, const float*, const float*,
                                           const int32_t*, const double*, double, double, bool,
                                           float*, float*, float*, float*, float*, const double*);
+template void grad_newton_g<float, float, float>(plc_ctx*, const float*, const double*,
+                                                 const int32_t*, double, float*, float*, float*,
+                                                 float*, bool);
+template void newton_update_g<float, float>(plc_ctx*, const float*, const float*, const float*,
+                                            const float*, const float*, const float*,
+                                            const int32_t*, const double*, double, double, bool,
+                                            float*, float*, float*, float*, float*);
+template void boundary_step<float, float>(plc_ctx*, const float*, const float*, const int32_t*);
 template void cg_hv<float>(plc_ctx*, const float*, const float*, float*, float*, bool);
 template void vjp_amplitude<float>(plc_ctx*, const double*, const float*);
+template void lsq_init<float>(plc_ctx*, const int32_t*, const double*, double, float*, float*,
+                              bool);
 template void cg_init<float>(plc_ctx*, const double*, const float*, float*, bool);
 template void cg_update<float>(plc_ctx*, float*, float*, const float*, const float*, const float*,
                                bool, double, int);

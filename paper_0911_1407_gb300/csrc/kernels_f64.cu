@@ -24,8 +24,28 @@ template void newton_update<double, float>(plc_ctx*, const double*, const double
                                            const int32_t*, const double*, double, double, bool,
                                            double*, double*, double*, float*, float*,
                                            const double*);
+template void grad_newton_g<double, double, double>(plc_ctx*, const double*, const double*,
+                                                    const int32_t*, double, double*, double*,
+                                                    double*, double*, bool);
+template void grad_newton_g<double, double, float>(plc_ctx*, const double*, const double*,
+                                                   const int32_t*, double, double*, double*,
+                                                   float*, float*, bool);
+template void newton_update_g<double, double>(plc_ctx*, const double*, const double*,
+                                              const double*, const double*, const double*,
+                                              const double*, const int32_t*, const double*,
+                                              double, double, bool, double*, double*, double*,
+                                              double*, double*);
+template void newton_update_g<double, float>(plc_ctx*, const double*, const double*,
+                                             const double*, const float*, const float*,
+                                             const float*, const int32_t*, const double*, double,
+                                             double, bool, double*, double*, double*, float*,
+                                             float*);
+template void boundary_step<double, double>(plc_ctx*, const double*, const double*, const int32_t*);
+template void boundary_step<double, float>(plc_ctx*, const double*, const float*, const int32_t*);
 template void cg_hv<double>(plc_ctx*, const double*, const double*, double*, double*, bool);
 template void vjp_amplitude<double>(plc_ctx*, const double*, const double*);
+template void lsq_init<double>(plc_ctx*, const int32_t*, const double*, double, double*, double*,
+                              bool);
 template void cg_init<double>(plc_ctx*, const double*, const double*, double*, bool);
 template void cg_update<double>(plc_ctx*, double*, double*, const double*, const double*,
                                 const double*, bool, double, int);

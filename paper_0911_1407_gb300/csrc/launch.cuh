@@ -176,6 +176,14 @@ void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, dou
                   FinGrad{}, 0, nullptr, true);
 }
 
+template <typename T, typename TS, typename TC>
+void grad_newton_g(plc_ctx* c, const TS* delta, const double* w, const int32_t* N, double nbar,
+                   T* y, T* g, TC* D, TC* r, bool jac) {
+  run_pipeline<T>(c, ProShift<T, TS>{delta, 0.0},
+                  EpiGradG<T, TS, TC>{delta, w, N, nbar, y, g, D, r, c->jac_c, jac ? 1 : 0},
+                  FinGrad{}, 0, nullptr, true);
+}
+
 template <typename T> void cg_hv(plc_ctx* c, const T* r, const T* D, T* p, T* Hp, bool jac) {
   const int* done = &c->sc->done;
   if (jac)
@@ -193,6 +201,25 @@ template <typename TL> void vjp_amplitude(plc_ctx* c, const double* s, const TL*
 
 inline int pw_blocks(plc_ctx* c) { return pointwise_blocks((long long)c->n3(), c->sms); }
 
+template <typename T, typename TC>
+void newton_update_g(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
+                     const TC* D, const int32_t* N, const double* w, double nbar, double tau,
+                     bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2) {
+  LaunchScope ls(c, sizeof(T) == 4 ? S_NEWTON_UPDATE32 : S_NEWTON_UPDATE64);
+  k_newton_update_g<T, TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(
+      s, y, g, r, xi, D, N, w, nbar, tau, c->jac_c, jac ? 1 : 0, s2, y2, g2, D2, r2, c->n3(),
+      red_args(c));
+  check(cudaGetLastError(), "k_newton_update_g");
+}
+
+template <typename T, typename TC>
+void boundary_step(plc_ctx* c, const T* delta, const TC* xi, const int32_t* N) {
+  LaunchScope ls(c, S_BOUNDARY);
+  k_boundary<T, TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(delta, xi, N, c->n3(), red_args(c));
+  check(cudaGetLastError(), "k_boundary");
+}
+
+
 template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC* r, bool jac) {
   const int nb = pw_blocks(c);
   LaunchScope ls(c, S_CG_INIT);
@@ -203,6 +230,19 @@ template <typename TC> void cg_init(plc_ctx* c, const double* b, const TC* D, TC
     k_cg_init<TC, double, false><<<nb, kThreads, 0, c->stream>>>(b, D, (TC)c->jac_c, r, c->n3(),
                                                                   red_args(c));
   check(cudaGetLastError(), "k_cg_init");
+}
+
+template <typename TC> void lsq_init(plc_ctx* c, const int32_t* N, const double* w, double nbar,
+                                     TC* D, TC* r, bool jac) {
+  const int nb = pw_blocks(c);
+  LaunchScope ls(c, S_CG_INIT);
+  if (jac)
+    k_lsq_init<TC, true><<<nb, kThreads, 0, c->stream>>>(N, w, nbar, (TC)c->jac_c, D, r,
+                                                         c->n3(), red_args(c));
+  else
+    k_lsq_init<TC, false><<<nb, kThreads, 0, c->stream>>>(N, w, nbar, (TC)c->jac_c, D, r,
+                                                          c->n3(), red_args(c));
+  check(cudaGetLastError(), "k_lsq_init");
 }
 
 template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, const TC* Hp,

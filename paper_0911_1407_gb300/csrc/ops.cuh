@@ -334,6 +334,87 @@ template <typename T, typename TS, typename TW, typename TC> struct EpiGrad {
   }
 };
 
+// ----------------------- Gaussian prior, Poisson likelihood -----------------
+// One cell of the Gaussian-prior model (Sec. 2.2.2, Eq. MAPG; gradient and
+// Hessian of Sec. 3.1.1 without the factor S): with u = 1 + delta,
+//   g = y + nbar w - N / u,   D = N / u^2,
+//   -ln P = 1/2 delta^T y + sum [nbar w u - N ln u],
+// y = S^-1 delta.  The sums mirror the lognormal model's, with ln u in the
+// place of s: {delta y, nbar w u - N ln u, g^2, N ln u, N |ln u|, r M^-1 r}.
+// A cell with N > 0 and u <= 0 lies outside the domain: its likelihood term
+// is +inf.
+template <typename T, typename TC>
+__device__ __forceinline__ void gauss_cell(T delta, T wt, T ni, T nb, T y, TC c, int jac,
+                                           typename AccOf<T>::type* acc, T& gi, T& d) {
+  const T u = (T)1 + delta;
+  const bool occ = ni > (T)0;
+  const T inv = (T)1 / u;
+  const T nio = occ ? ni * inv : (T)0;
+  gi = y + nb * wt - nio;
+  d = nio * inv;
+  const T lu = occ ? (u > (T)0 ? ni * log(u) : (T)INFINITY) : (T)0;
+  acc[0].add(delta * y);
+  acc[1].add(nb * wt * u - lu);
+  acc[2].add(gi * gi);
+  acc[3].add(lu);
+  acc[4].add(lu < (T)0 ? -lu : lu);
+  const TC gc = (TC)gi;
+  acc[5].add((T)(jac ? gc * jacobi(gc, (TC)d, c) : gc * gc));
+}
+
+// Gradient epilogue of the Gaussian-prior model (the prologue passes delta:
+// ProShift with mu = 0).  Writes y, g (T), D, r = -g (TC); sums as EpiGrad.
+template <typename T, typename TS, typename TC> struct EpiGradG {
+  static constexpr int NV = 6;
+  static constexpr unsigned MAXMASK = 0;
+  using Acc = typename AccOf<T>::type;
+  const TS* s;           // delta
+  const double* w;       // may be null
+  const int32_t* N;
+  double nbar;
+  T* yout;
+  T* g;
+  TC* D;
+  TC* r;
+  double c;
+  int jac;
+  __device__ void prefetch(size_t i, unsigned cnt) const {
+    prefetch_l2(s + i, cnt * sizeof(TS));
+    prefetch_l2(N + i, cnt * sizeof(int32_t));
+    if (w) prefetch_l2(w + i, cnt * sizeof(double));
+  }
+  __device__ void operator()(size_t i, T y, Acc* acc) const {
+    T gi, d;
+    gauss_cell<T, TC>((T)__ldg(s + i), w ? (T)__ldg(w + i) : (T)1, (T)__ldg(N + i), (T)nbar, y,
+                      (TC)c, jac, acc, gi, d);
+    if (yout) yout[i] = y;
+    if (g) g[i] = gi;
+    if (D) D[i] = (TC)d;
+    if (r) r[i] = (TC)(-gi);
+  }
+  __device__ void vec4(size_t i, const V4<T>& y, Acc* acc) const {
+    const V4<TS> sv = ld4(s + i);
+    const V4<int32_t> nv = ld4(N + i);
+    V4<double> wv{{1.0, 1.0, 1.0, 1.0}};
+    if (w) wv = ld4(w + i);
+    V4<T> gv;
+    V4<TC> dv, rv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      T gi, d;
+      gauss_cell<T, TC>((T)sv.v[j], (T)wv.v[j], (T)nv.v[j], (T)nbar, y.v[j], (TC)c, jac, acc, gi,
+                        d);
+      gv.v[j] = gi;
+      dv.v[j] = (TC)d;
+      rv.v[j] = (TC)(-gi);
+    }
+    if (yout) st4(yout + i, y);
+    if (g) st4(g + i, gv);
+    if (D) st4(D + i, dv);
+    if (r) st4(r + i, rv);
+  }
+};
+
 // sum lam_i y_i, y = S^-1 x.
 template <typename T, typename TL> struct EpiDot {
   static constexpr int NV = 1;
@@ -405,6 +486,47 @@ struct FinAlpha {
 };
 
 // ------------------------------ CG kernels --------------------------------
+// CG scalars at the start of a solve from x = 0 (t = {r^T M^-1 r, r^T r}).
+struct FinCgStart {
+  __device__ void operator()(const double* t, DevScalars* sc) const {
+    sc->rz = t[0];
+    sc->rr = t[1];
+    sc->bnorm2 = t[1];
+    sc->iter = 0;
+    sc->beta = 0.0;
+    sc->alpha = 0.0;
+    sc->breakdown = 0;
+    sc->xb = 0.0;
+    sc->xHx = 0.0;
+    sc->xmax = 0.0;
+    sc->done = t[1] <= 0.0 ? 1 : 0;
+  }
+};
+
+// LSQ-Wiener filter (Sec. 4.1.1, Eq. WF, unity bias): the diagonal
+// D = nbar w of (S^-1 + diag(nbar w)) delta = N - nbar w and the CG start
+// r = N - nbar w from delta = 0.
+template <typename TC, bool JAC>
+__global__ void __launch_bounds__(kThreads)
+k_lsq_init(const int32_t* __restrict__ N, const double* __restrict__ w, double nbar, TC c,
+           TC* __restrict__ D, TC* __restrict__ r, size_t n3, RedArgs ra) {
+  typename AccOf<TC>::type acc[2];
+  acc[0].init(false);
+  acc[1].init(false);
+  const TC nb = (TC)nbar;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const TC d = w ? (TC)(nbar * w[i]) : nb;
+    const TC ri = (TC)N[i] - d;
+    D[i] = d;
+    r[i] = ri;
+    const TC zi = JAC ? jacobi(ri, d, c) : ri;
+    acc[0].add(ri * zi);
+    acc[1].add(ri * ri);
+  }
+  block_reduce_finish_acc<2, 0u>(acc, ra, FinCgStart{});
+}
+
 // Start CG on H x = b from x = 0: r = b, rz = r^T M^-1 r, rr = r^T r.
 template <typename TC, typename TB, bool JAC>
 __global__ void __launch_bounds__(kThreads)
@@ -422,22 +544,7 @@ k_cg_init(const TB* __restrict__ b, const TC* __restrict__ D, TC c, TC* __restri
     a1.add(ri * ri);
   }
   typename AccOf<TC>::type acc[2] = {a0, a1};
-  struct Fin {
-    __device__ void operator()(const double* t, DevScalars* sc) const {
-      sc->rz = t[0];
-      sc->rr = t[1];
-      sc->bnorm2 = t[1];
-      sc->iter = 0;
-      sc->beta = 0.0;
-      sc->alpha = 0.0;
-      sc->breakdown = 0;
-      sc->xb = 0.0;
-      sc->xHx = 0.0;
-      sc->xmax = 0.0;
-      sc->done = t[1] <= 0.0 ? 1 : 0;
-    }
-  };
-  block_reduce_finish_acc<2, 0u>(acc, ra, Fin{});
+  block_reduce_finish_acc<2, 0u>(acc, ra, FinCgStart{});
 }
 
 // x += alpha p (x = alpha p on the first step, so x needs no clearing),
@@ -574,6 +681,81 @@ k_convert(const TS* __restrict__ src, TD* __restrict__ dst, size_t n3) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
        i += (size_t)gridDim.x * blockDim.x)
     dst[i] = (TD)src[i];
+}
+
+// Line-search trial of the Gaussian-prior model, without an FFT (as
+// k_newton_update): delta' = delta + tau xi, y' = y + tau S^-1 xi with
+// S^-1 xi = (b - r) - D xi from the CG, then g', D', r' and the sums.
+template <typename T, typename TC>
+__global__ void __launch_bounds__(kThreads)
+k_newton_update_g(const T* __restrict__ s, const T* __restrict__ y, const T* __restrict__ g,
+                  const TC* __restrict__ r, const TC* __restrict__ xi, const TC* __restrict__ D,
+                  const int32_t* __restrict__ N, const double* __restrict__ w, double nbar,
+                  double tau, double c, int jac, T* __restrict__ s2, T* __restrict__ y2,
+                  T* __restrict__ g2, TC* __restrict__ D2, TC* __restrict__ r2, size_t n3,
+                  RedArgs ra) {
+  using Acc = typename AccOf<T>::type;
+  Acc acc[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) acc[j].init(false);
+  const T tt = (T)tau, nb = (T)nbar;
+  const TC cc = (TC)c;
+  const size_t step = (size_t)gridDim.x * blockDim.x * 4;
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < n3; i += step) {
+    const V4<TC> xv = ld4(xi + i), rv = ld4(r + i), dv = ld4(D + i);
+    const V4<T> sv = ld4(s + i), yv = ld4(y + i), gv = ld4(g + i);
+    const V4<int32_t> nv = ld4(N + i);
+    V4<double> wv{{1.0, 1.0, 1.0, 1.0}};
+    if (w) wv = ld4(w + i);
+    V4<T> so, yo, go;
+    V4<TC> dout, rout;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const TC sinv_xi = (TC)(-gv.v[j]) - rv.v[j] - dv.v[j] * xv.v[j];
+      const T yn = yv.v[j] + tt * (T)sinv_xi;
+      const T sn = sv.v[j] + tt * (T)xv.v[j];
+      T gn, d;
+      gauss_cell<T, TC>(sn, (T)wv.v[j], (T)nv.v[j], nb, yn, cc, jac, acc, gn, d);
+      so.v[j] = sn;
+      yo.v[j] = yn;
+      go.v[j] = gn;
+      dout.v[j] = (TC)d;
+      rout.v[j] = (TC)(-gn);
+    }
+    st4(s2 + i, so);
+    st4(y2 + i, yo);
+    st4(g2 + i, go);
+    st4(D2 + i, dout);
+    st4(r2 + i, rout);
+  }
+  block_reduce_finish_acc<6, 0u>(acc, ra, FinGrad{});
+}
+
+// Fraction to the boundary of the Gaussian-prior model: the largest
+// -xi / (1 + delta) over cells with N > 0 and xi < 0 (0 if none), so that
+// any tau < 1 / that keeps 1 + delta + tau xi > 0 where the likelihood has
+// its logarithm.  Stored in the device scalars' bmax.
+template <typename T, typename TC>
+__global__ void __launch_bounds__(kThreads)
+k_boundary(const T* __restrict__ s, const TC* __restrict__ xi, const int32_t* __restrict__ N,
+           size_t n3, RedArgs ra) {
+  typename AccOf<T>::type acc[1];
+  acc[0].init(true);
+  const size_t step = (size_t)gridDim.x * blockDim.x * 4;
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < n3; i += step) {
+    const V4<T> sv = ld4(s + i);
+    const V4<TC> xv = ld4(xi + i);
+    const V4<int32_t> nv = ld4(N + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (nv.v[j] > 0 && xv.v[j] < (TC)0) acc[0].max((T)(-xv.v[j]) / ((T)1 + sv.v[j]));
+  }
+  struct Fin {
+    __device__ void operator()(const double* t, DevScalars* sc) const {
+      sc->bmax = t[0] > 0.0 ? t[0] : 0.0;
+    }
+  };
+  block_reduce_finish_acc<1, 1u>(acc, ra, Fin{});
 }
 
 }  // namespace plc

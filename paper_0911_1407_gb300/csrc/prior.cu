@@ -55,7 +55,7 @@ const char* const kSiteNames[S_NSITES] = {
     "grad_xf_f32", "grad_yf_f32", "grad_z_f32", "grad_yi_f32", "grad_xi_f32",
     "grad_xf_ff", "grad_yf_ff", "grad_z_ff", "grad_yi_ff", "grad_xi_ff",
     "cg_init", "cg_update_f64", "cg_update_f32", "newton_update_f64", "newton_update_f32",
-    "diag", "convert", "setup"};
+    "diag", "convert", "setup", "boundary"};
 
 constexpr int kProfSlots = 512;
 

@@ -88,11 +88,45 @@ struct State {
   void* r;
 };
 
+// The two models of the solve.  Lognormal prior (Sec. 2.3, Eq. MAPLNUB):
+// unknown s = ln(1 + delta), steps capped by max |tau xi| <= step_cap.
+// Gaussian prior (Sec. 2.2.2, Eq. MAPG): unknown delta, steps kept inside
+// the domain 1 + delta > 0 (cells with N > 0) by the fraction to the
+// boundary, tau <= 0.99 / max(-xi / (1 + delta)).
+struct Lognormal {
+  static constexpr bool kBoundary = false;
+  template <typename T, typename TS, typename TC>
+  static void gradient(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar,
+                       T* y, T* g, TC* D, TC* r, bool jac) {
+    grad_newton<T, TS, TC>(c, s, w, N, nbar, y, g, D, r, jac);
+  }
+  template <typename T, typename TC>
+  static void trial(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
+                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,
+                    bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2) {
+    newton_update<T, TC>(c, s, y, g, r, xi, D, N, w, nbar, tau, jac, s2, y2, g2, D2, r2);
+  }
+};
+struct GaussPrior {
+  static constexpr bool kBoundary = true;
+  template <typename T, typename TS, typename TC>
+  static void gradient(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar,
+                       T* y, T* g, TC* D, TC* r, bool jac) {
+    grad_newton_g<T, TS, TC>(c, s, w, N, nbar, y, g, D, r, jac);
+  }
+  template <typename T, typename TC>
+  static void trial(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
+                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,
+                    bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2) {
+    newton_update_g<T, TC>(c, s, y, g, r, xi, D, N, w, nbar, tau, jac, s2, y2, g2, D2, r2);
+  }
+};
+
 }  // namespace
 
-template <typename TC>
-plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar, double* s_out,
-                      const plc_opts& o, plc_stats* st) {
+template <typename Model, typename TC>
+plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, double nbar,
+                            double* s_out, const plc_opts& o, plc_stats* st) {
   constexpr bool kMixed = std::is_same<TC, float>::value;
   const auto t0 = std::chrono::steady_clock::now();
   void** F = c->wf;
@@ -108,12 +142,14 @@ plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar
   // y, g, D, r and the sums at cur.s through the FFT (phase precision)
   auto fft_gradient = [&]() {
     if (fp64) {
-      grad_newton<double, double, TC>(c, as<double>(cur.s), w, N, nbar, as<double>(cur.y),
-                                      as<double>(cur.g), as<TC>(cur.D), as<TC>(cur.r), jac);
+      Model::template gradient<double, double, TC>(c, as<double>(cur.s), w, N, nbar,
+                                                   as<double>(cur.y), as<double>(cur.g),
+                                                   as<TC>(cur.D), as<TC>(cur.r), jac);
       S.grad_ffts_fp64 += 1;
     } else if constexpr (kMixed) {
-      grad_newton<float, float, float>(c, as<float>(cur.s), w, N, nbar, as<float>(cur.y),
-                                       as<float>(cur.g), as<float>(cur.D), as<float>(cur.r), jac);
+      Model::template gradient<float, float, float>(c, as<float>(cur.s), w, N, nbar,
+                                                    as<float>(cur.y), as<float>(cur.g),
+                                                    as<float>(cur.D), as<float>(cur.r), jac);
     }
     read_scalars(c);
     S.grad_evals += 1;
@@ -122,15 +158,16 @@ plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar
   };
   auto trial = [&](double tau) {
     if (fp64) {
-      newton_update<double, TC>(c, as<double>(cur.s), as<double>(cur.y), as<double>(cur.g),
-                                as<TC>(cur.r), x, as<TC>(cur.D), N, w, nbar, tau, jac,
-                                as<double>(alt.s), as<double>(alt.y), as<double>(alt.g),
-                                as<TC>(alt.D), as<TC>(alt.r));
+      Model::template trial<double, TC>(c, as<double>(cur.s), as<double>(cur.y),
+                                        as<double>(cur.g), as<TC>(cur.r), x, as<TC>(cur.D), N, w,
+                                        nbar, tau, jac, as<double>(alt.s), as<double>(alt.y),
+                                        as<double>(alt.g), as<TC>(alt.D), as<TC>(alt.r));
     } else if constexpr (kMixed) {
-      newton_update<float, float>(c, as<float>(cur.s), as<float>(cur.y), as<float>(cur.g),
-                                  as<float>(cur.r), x, as<float>(cur.D), N, w, nbar, tau, jac,
-                                  as<float>(alt.s), as<float>(alt.y), as<float>(alt.g),
-                                  as<float>(alt.D), as<float>(alt.r));
+      Model::template trial<float, float>(c, as<float>(cur.s), as<float>(cur.y),
+                                          as<float>(cur.g), as<float>(cur.r), x,
+                                          as<float>(cur.D), N, w, nbar, tau, jac,
+                                          as<float>(alt.s), as<float>(alt.y), as<float>(alt.g),
+                                          as<float>(alt.D), as<float>(alt.r));
     }
     read_scalars(c);
     S.grad_evals += 1;
@@ -188,7 +225,15 @@ plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar
     // 2. step length of Eq. (New5); b = -g, so xi^T g = -xi^T b
     const double xg = -c->sc_host->xb, xHx = c->sc_host->xHx, xmax = c->sc_host->xmax;
     double tau = -xg / xHx;
-    if (tau * xmax > o.step_cap) tau = o.step_cap / xmax;
+    if constexpr (Model::kBoundary) {
+      if (fp64) boundary_step<double, TC>(c, as<double>(cur.s), x, N);
+      else if constexpr (kMixed) boundary_step<float, float>(c, as<float>(cur.s), x, N);
+      read_scalars(c);
+      const double bmax = c->sc_host->bmax;
+      if (bmax > 0.0) tau = std::min(tau, 0.99 / bmax);
+    } else {
+      if (tau * xmax > o.step_cap) tau = o.step_cap / xmax;
+    }
     // 3. Armijo backtracking on element-wise trial points
     const double eps = fp64 ? 1e-13 : 1e-6;     // rounding level of f
     const double f0 = gs.f(), scale = gs.scale();
@@ -258,10 +303,72 @@ plc_status map_vjp(plc_ctx* c, const double* s_map, const double* w, double nbar
   return status;
 }
 
+// LSQ-Wiener filter (Sec. 4.1.1, Eq. WF with unity bias; Table 1): one
+// Jacobi-preconditioned CG solve of (S^-1 + diag(nbar w)) delta = N - nbar w
+// from delta = 0 to relative residual tol, in the CG precision of the
+// context (FP32 for PLC_MIXED, so a relative residual of about 1e-6 at best).
+template <typename TC>
+plc_status wiener_lsq(plc_ctx* c, const int32_t* N, const double* w, double nbar, double* delta,
+                      const plc_opts& o, plc_stats* st) {
+  constexpr bool kMixed = std::is_same<TC, float>::value;
+  const auto t0 = std::chrono::steady_clock::now();
+  void** F = c->wf;
+  TC* D = as<TC>(F[6]);
+  TC* r = as<TC>(F[8]);
+  TC* x = as<TC>(F[10]);
+  TC* p = as<TC>(F[11]);
+  TC* Hp = as<TC>(F[12]);
+  const bool jac = o.precond == 1;
+  reset_ticket(c);
+  lsq_init<TC>(c, N, w, nbar, D, r, jac);
+  const double rtol2 = o.tol * o.tol;
+  const int iters = run_cg<TC>(c, x, r, p, Hp, D, jac, rtol2, o.max_cg, o.cg_chunk, o.cg_chunk);
+  const DevScalars& h = *c->sc_host;
+  plc_status status = PLC_OK;
+  if (h.breakdown && iters == 0) status = PLC_ERR_CG_BREAKDOWN;
+  else if (h.rr > rtol2 * h.bnorm2) status = PLC_ERR_NOT_CONVERGED;
+  if (iters == 0)            // N = nbar w everywhere: delta = 0
+    check(cudaMemsetAsync(x, 0, sizeof(TC) * c->n3(), c->stream), "clear");
+  if constexpr (kMixed) convert<double, float>(c, x, delta);
+  else check(cudaMemcpyAsync(delta, x, sizeof(double) * c->n3(), cudaMemcpyDeviceToDevice, c->stream),
+             "copy delta");
+  check(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (st) {
+    *st = plc_stats{};
+    st->cg_iters = iters;
+    st->hv_count = iters;
+    st->grad_rel = h.bnorm2 > 0 ? std::sqrt(h.rr / h.bnorm2) : 0.0;
+    st->g0_norm = std::sqrt(h.bnorm2);
+    st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+template plc_status wiener_lsq<double>(plc_ctx*, const int32_t*, const double*, double, double*,
+                                       const plc_opts&, plc_stats*);
+template plc_status wiener_lsq<float>(plc_ctx*, const int32_t*, const double*, double, double*,
+                                      const plc_opts&, plc_stats*);
+
+template <typename TC>
+plc_status newton_map(plc_ctx* c, const int32_t* N, const double* w, double nbar, double* s,
+                      const plc_opts& o, plc_stats* st) {
+  return newton_map_model<Lognormal, TC>(c, N, w, nbar, s, o, st);
+}
+
+template <typename TC>
+plc_status gauss_map(plc_ctx* c, const int32_t* N, const double* w, double nbar, double* delta,
+                     const plc_opts& o, plc_stats* st) {
+  return newton_map_model<GaussPrior, TC>(c, N, w, nbar, delta, o, st);
+}
+
 template plc_status newton_map<double>(plc_ctx*, const int32_t*, const double*, double, double*,
                                        const plc_opts&, plc_stats*);
 template plc_status newton_map<float>(plc_ctx*, const int32_t*, const double*, double, double*,
                                       const plc_opts&, plc_stats*);
+template plc_status gauss_map<double>(plc_ctx*, const int32_t*, const double*, double, double*,
+                                      const plc_opts&, plc_stats*);
+template plc_status gauss_map<float>(plc_ctx*, const int32_t*, const double*, double, double*,
+                                     const plc_opts&, plc_stats*);
 template plc_status map_vjp<double>(plc_ctx*, const double*, const double*, double, const double*,
                                     double*, double*, const plc_opts&, plc_stats*);
 template plc_status map_vjp<float>(plc_ctx*, const double*, const double*, double, const double*,

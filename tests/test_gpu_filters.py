@@ -1,0 +1,80 @@
+"""GPU parity of the LSQ-Wiener filter (plc_wiener_lsq) against the oracle.
+
+Bars: FP64 relative L2 <= 1e-10 of the oracle's solution (both to relative
+residual 1e-12); PLC_MIXED (FP32 CG) relative L2 <= 1e-5 at residual 1e-6.
+At the full workload sizes the GPU solution's residual is taken with the
+oracle's own FP64 operator.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import filters, plc as orc
+from paper_0911_1407_gb300 import mocks
+from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plc():
+    return ensure_lib()
+
+
+def _ctx(plc, m, precision):
+    c = plc.Context(m.n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    return c
+
+
+def _problem(m):
+    return orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab)
+
+
+@pytest.mark.parametrize("n,sel", [(24, "radial_masked"), (32, "uniform"), (48, "radial_masked"),
+                                   (18, "uniform")])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_lsq_matches_oracle(plc, n, sel, precision):
+    m = small_mock(n, sel, sigma=1.3, nbar=0.8)
+    ref, cg = filters.wiener_lsq(_problem(m), rtol=1e-13)
+    c = _ctx(plc, m, precision)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    d, st, stats = c.wiener_lsq(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=tol)
+    assert st == 0 and stats["grad_rel"] <= tol
+    assert rel_l2(host(d), ref) <= (1e-10 if precision == "fp64" else 1e-5)
+
+
+def test_lsq_diagonal_prior_closed_form(plc):
+    n, box, sigma2 = 16, 80.0, 0.9
+    rng = np.random.default_rng(3)
+    N = rng.poisson(2.0, size=(n, n, n)).astype(np.int32)
+    w = rng.uniform(0.05, 1.0, size=(n, n, n))
+    nbar = 1.6
+    k = np.array([0.5 * 2 * math.pi / box, 2 * math.sqrt(3) * math.pi * n / box])
+    P = np.full(2, sigma2 * box ** 3 / n ** 3)
+    c = plc.Context(n, box, "fp64")
+    c.set_prior(k, P, 0.0, 1.0 / sigma2)
+    d, st, _ = c.wiener_lsq(dev(N, torch.int32), dev(w, torch.float64), nbar, tol=1e-13)
+    exact = filters.wiener_closed_form_diagonal(N, w, nbar, sigma2)
+    assert np.max(np.abs(host(d) - exact)) <= 1e-11 * np.max(np.abs(exact))
+
+
+@pytest.mark.parametrize("key,precision", [("selection128", "fp64"), ("selection128", "mixed"),
+                                           ("production256", "mixed")])
+def test_lsq_full_size_residual_by_the_oracle(plc, key, precision):
+    m = mocks.make_mock(mocks.WORKLOADS[key])
+    c = _ctx(plc, m, precision)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    d, st, stats = c.wiener_lsq(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=tol)
+    assert st == 0
+    p = _problem(m)
+    delta = host(d)
+    wn = p.wn * np.ones(m.N.shape)
+    b = m.N - wn
+    res = orc.apply_Sinv(delta, p.inv_lam) + wn * delta - b
+    # FP64: the CG's recursive residual and the true one agree to rounding;
+    # FP32 CG: the true residual sits at the FP32 rounding level
+    bar = 2.0 * tol if precision == "fp64" else 1e-5
+    assert np.linalg.norm(res) / np.linalg.norm(b) <= bar
