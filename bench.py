@@ -544,6 +544,18 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
         lsq[prec] = {"ms": e0.elapsed_time(e1), "cg_iters": st["cg_iters"],
                      "rel_residual": st["grad_rel"]}
     line["lsq_wiener"] = lsq
+    # the Gaussian-prior Poisson MAP (Eq. MAPG) on the same data, from delta = 0
+    dg = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    ctx.gauss_map(N_dev, None, m.nbar, delta=dg, tol=TOL)
+    dg.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rg = ctx.gauss_map(N_dev, None, m.nbar, delta=dg, tol=TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    line["gauss_prior_map"] = {"ms": e0.elapsed_time(e1), "precision": "mixed",
+                               **{k: rg.stats[k] for k in ("newton_iters", "cg_iters",
+                                                           "grad_ffts", "grad_rel")}}
     batch_extra(plc, line)
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:

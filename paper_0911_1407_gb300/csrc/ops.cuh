@@ -348,8 +348,10 @@ __device__ __forceinline__ void gauss_cell(T delta, T wt, T ni, T nb, T y, TC c,
                                            typename AccOf<T>::type* acc, T& gi, T& d) {
   const T u = (T)1 + delta;
   const bool occ = ni > (T)0;
-  const T inv = (T)1 / u;
-  const T nio = occ ? ni * inv : (T)0;
+  // 1/u only where the likelihood has its logarithm (an empty cell may sit
+  // at u = 0 exactly)
+  const T inv = occ ? (T)1 / u : (T)0;
+  const T nio = ni * inv;
   gi = y + nb * wt - nio;
   d = nio * inv;
   const T lu = occ ? (u > (T)0 ? ni * log(u) : (T)INFINITY) : (T)0;

@@ -78,3 +78,80 @@ def test_lsq_full_size_residual_by_the_oracle(plc, key, precision):
     # FP32 CG: the true residual sits at the FP32 rounding level
     bar = 2.0 * tol if precision == "fp64" else 1e-5
     assert np.linalg.norm(res) / np.linalg.norm(b) <= bar
+
+
+# ------------------------- Gaussian prior, Poisson likelihood ---------------
+
+_GAUSS_CACHE = {}
+
+
+def _gauss_ref(key, m, tol=1e-12):
+    if key not in _GAUSS_CACHE:
+        _GAUSS_CACHE[key] = filters.gauss_map(_problem(m), tol=tol)
+    return _GAUSS_CACHE[key]
+
+
+def _gauss_mock(key):
+    if key == "g24":
+        return small_mock(24, "radial_masked", sigma=1.2, nbar=1.0)
+    if key == "g32":
+        return small_mock(32, "uniform", sigma=1.0, nbar=2.0)
+    raise KeyError(key)
+
+
+@pytest.mark.parametrize("key", ["g24", "g32"])
+def test_gauss_map_fp64_matches_oracle(plc, key):
+    m = _gauss_mock(key)
+    ref = _gauss_ref(key, m)
+    assert ref.converged
+    c = _ctx(plc, m, "fp64")
+    r = c.gauss_map(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=1e-12)
+    assert r.stats["grad_rel"] < 1e-12
+    d = host(r.s)
+    err = np.abs(d - ref.delta) / np.maximum(np.abs(ref.delta), 1.0)
+    assert err.max() <= 1e-10
+    assert np.all(1.0 + d[m.N > 0] > 0.0)
+
+
+@pytest.mark.parametrize("key", ["g24", "g32"])
+def test_gauss_map_mixed_matches_oracle(plc, key):
+    m = _gauss_mock(key)
+    ref = _gauss_ref(key, m)
+    c = _ctx(plc, m, "mixed")
+    r = c.gauss_map(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=1e-6)
+    assert r.stats["grad_rel"] < 1e-6
+    d = host(r.s)
+    assert np.max(np.abs(d - ref.delta) / np.maximum(np.abs(ref.delta), 1.0)) <= 1e-4
+    assert rel_l2(d, ref.delta) <= 1e-5
+
+
+def test_gauss_map_diagonal_prior_closed_form(plc):
+    n, box, sigma2 = 16, 80.0, 0.9
+    rng = np.random.default_rng(13)
+    N = rng.poisson(2.0, size=(n, n, n)).astype(np.int32)
+    N[0, 0, 0] = 50
+    w = rng.uniform(0.05, 1.0, size=(n, n, n))
+    nbar = 1.6
+    k = np.array([0.5 * 2 * math.pi / box, 2 * math.sqrt(3) * math.pi * n / box])
+    P = np.full(2, sigma2 * box ** 3 / n ** 3)
+    c = plc.Context(n, box, "fp64")
+    c.set_prior(k, P, 0.0, 1.0 / sigma2)
+    r = c.gauss_map(dev(N, torch.int32), dev(w, torch.float64), nbar, tol=1e-13)
+    exact = filters.gauss_closed_form_diagonal(N, w, nbar, sigma2)
+    err = np.abs(host(r.s) - exact) / np.maximum(np.abs(exact), 1.0)
+    assert err.max() <= 1e-10
+
+
+@pytest.mark.parametrize("key,precision", [("selection128", "fp64"), ("selection128", "mixed"),
+                                           ("production256", "mixed")])
+def test_gauss_map_full_size_is_a_map_for_the_oracle(plc, key, precision):
+    m = mocks.make_mock(mocks.WORKLOADS[key])
+    c = _ctx(plc, m, precision)
+    r = c.gauss_map(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=1e-6)
+    d = host(r.s)
+    p = _problem(m)
+    g0 = np.linalg.norm(filters.gauss_gradient(np.zeros(m.N.shape), p))
+    rel = np.linalg.norm(filters.gauss_gradient(d, p)) / g0
+    assert rel < 1e-6
+    assert abs(rel - r.stats["grad_rel"]) <= 1e-3 * r.stats["grad_rel"]
+    assert np.all(1.0 + d[m.N > 0] > 0.0)
