@@ -556,6 +556,31 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     line["gauss_prior_map"] = {"ms": e0.elapsed_time(e1), "precision": "mixed",
                                **{k: rg.stats[k] for k in ("newton_iters", "cg_iters",
                                                            "grad_ffts", "grad_rel")}}
+    # reconstruction quality against the true field (r and D_Euc, Sec. 4.1.2)
+    # and the matter statistics of ln(1 + delta) after 10 Mpc/h smoothing
+    d_true = torch.expm1(torch.from_numpy(m.s_true).cuda())
+    ests = {"lognormal_map": torch.expm1(s_mixed), "gauss_prior_map": dg,
+            "lsq_wiener": ctx.wiener_lsq(N_dev, None, m.nbar, tol=1e-6)[0],
+            "inverse_weighting": N_dev.double() / m.nbar - 1.0}
+    quality = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for name, d in ests.items():
+        r, de = ctx.compare(d, d_true)
+        quality[name] = {"r": r, "d_euc": de}
+    t_cmp = (time.perf_counter() - t0) / len(ests)
+    sm = torch.empty_like(d_true)
+    for name, d in (("truth", d_true), ("lognormal_map", ests["lognormal_map"])):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.smooth(d, 10.0, out=sm)
+        t_smooth = time.perf_counter() - t0
+        _, outside, mom = ctx.log_stats(sm, -4.0, 0.2, 40)
+        quality.setdefault(name, {})["smoothed10"] = {
+            "mean": mom[0], "var": mom[1], "skewness": mom[2], "kurtosis": mom[3],
+            "invalid": outside[2]}
+    quality["ms"] = {"compare": 1e3 * t_cmp, "smooth": 1e3 * t_smooth}
+    line["reconstruction_quality"] = quality
     batch_extra(plc, line)
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:

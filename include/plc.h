@@ -198,6 +198,35 @@ plc_status plc_map_vjp(plc_ctx* ctx, const double* s_map, const void* w,
                        double nbar, const double* u, double* vjp_N,
                        double* vjp_lnA, const plc_opts* opts, plc_stats* stats);
 
+/* Quality measures of a reconstruction (Sec. 4.1.2; the paper compares
+ * estimates with the true matter field by these): the correlation
+ * coefficient r = sum a b / (sqrt(sum a^2) sqrt(sum b^2)) and the Euclidean
+ * distance D_Euc = sqrt(mean((a - b)^2)) of two double fields, reduced in
+ * FP64 (either output may be NULL, not both).  Synchronises the stream. */
+plc_status plc_compare(plc_ctx* ctx, const double* a, const double* b, double* r,
+                       double* d_euc);
+
+/* Gaussian smoothing on the periodic grid (Sec. 4.3.3 smooths with radii of
+ * 5 and 10 Mpc/h before the matter statistics): y = x convolved with a
+ * normalised Gaussian of radius `radius` (Mpc/h, >= 0), i.e. every Fourier
+ * mode multiplied by exp(-|k|^2 radius^2 / 2), |k| as for the prior.  x, y:
+ * double fields (may alias).  Transforms in float-float (about 48 bits) for
+ * lengths with a four-step schedule, FP64 otherwise; uses the solver work
+ * fields as scratch.  Needs no prior.  Synchronises the stream. */
+plc_status plc_smooth(plc_ctx* ctx, const double* x, double* y, double radius);
+
+/* Matter statistics of x = ln(1 + delta) (Sec. 4.3.3): counts[j] (host,
+ * nbins entries, 1 <= nbins <= 4096) of cells with x in
+ * [lo + j width, lo + (j+1) width) (bin index floor((x - lo) / width) in
+ * FP64), outside[3] = {below lo, at or above lo + nbins width, cells with
+ * 1 + delta <= 0}, and moments[4] = {mean, variance (population), skewness
+ * m3 / m2^(3/2), excess kurtosis m4 / m2^2 - 3} of x over the cells with
+ * 1 + delta > 0 (the paper defers these formulas to earlier work; these are
+ * the standard ones).  delta: double field.  Uses the solver work fields as
+ * scratch.  Synchronises the stream. */
+plc_status plc_log_stats(plc_ctx* ctx, const double* delta, double lo, double width, int nbins,
+                         long long* counts, long long* outside, double* moments);
+
 /* FFT schedule of the FP32 transforms (PLC_MIXED contexts; an aid to
  * performance, the paper has no counterpart).  A length n = f1 f2 with a
  * register four-step form can run it with the factors (f1, f2) or with the

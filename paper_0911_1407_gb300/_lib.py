@@ -25,7 +25,8 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
-           "plc_gauss_map", "plc_wiener_lsq", "plc_set_fft_schedule", "plc_autotune",
+           "plc_gauss_map", "plc_wiener_lsq", "plc_compare", "plc_smooth", "plc_log_stats",
+           "plc_set_fft_schedule", "plc_autotune",
            "plc_batch_create", "plc_batch_map", "plc_batch_destroy",
            "plc_profile_enable", "plc_profile_read", "plc_hessvec_noalloc", "plc_last_error",
            "plc_status_string"]
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_wiener_lsq": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_gauss_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_compare": (I, [P, P, P, DP, DP]),
+        "plc_smooth": (I, [P, P, P, D]),
+        "plc_log_stats": (I, [P, P, D, D, I, ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_longlong), DP]),
         "plc_set_fft_schedule": (I, [P, I, I]),
         "plc_autotune": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), DP]),
         "plc_batch_create": (I, [ctypes.POINTER(P), ctypes.POINTER(P), I]),
@@ -277,6 +282,31 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return out, st, stt.as_dict()
+
+    def compare(self, a, b):
+        """(r, D_Euc) of two float64 fields."""
+        r, d = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.plc_compare(self._h, _ptr(a, self.n, torch.float64, "a"),
+                                         _ptr(b, self.n, torch.float64, "b"), ctypes.byref(r),
+                                         ctypes.byref(d)))
+        return r.value, d.value
+
+    def smooth(self, x, radius: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Gaussian smoothing of a float64 field (radius in Mpc/h)."""
+        out = self.field(torch.float64) if out is None else out
+        self._check(self.lib.plc_smooth(self._h, _ptr(x, self.n, torch.float64, "x"),
+                                        _ptr(out, self.n, torch.float64, "y"), float(radius)))
+        return out
+
+    def log_stats(self, delta, lo: float, width: float, nbins: int):
+        """Histogram of ln(1 + delta), (below, above, invalid), moments."""
+        counts = (ctypes.c_longlong * int(nbins))()
+        outside = (ctypes.c_longlong * 3)()
+        mom = (ctypes.c_double * 4)()
+        self._check(self.lib.plc_log_stats(self._h, _ptr(delta, self.n, torch.float64, "delta"),
+                                           float(lo), float(width), int(nbins), counts, outside,
+                                           mom))
+        return np.array(counts[:], dtype=np.int64), tuple(outside[:]), tuple(mom[:])
 
     def set_fft_schedule(self, f1: int, f2: int):
         """FP32 line-transform schedule: four-step n = f1 f2, or (0, 0) Stockham."""

@@ -473,6 +473,52 @@ plc_status plc_map_vjp(plc_ctx* c, const double* s_map, const void* w, double nb
   });
 }
 
+plc_status plc_compare(plc_ctx* c, const double* a, const double* b, double* r, double* d_euc) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  PLC_TRY(need_field(c, a, "a", true));
+  PLC_TRY(need_field(c, b, "b", true));
+  if (!r && !d_euc) return fail(c, PLC_ERR_INVALID_ARG, "no output requested");
+  return guarded(c, [&]() -> plc_status {
+    double t[4];
+    plc::compare_fields(c, a, b, t);
+    if (r) *r = (t[1] > 0.0 && t[2] > 0.0) ? t[0] / (std::sqrt(t[1]) * std::sqrt(t[2])) : 0.0;
+    if (d_euc) *d_euc = std::sqrt(t[3] / (double)c->n3());
+    return PLC_OK;
+  });
+}
+
+plc_status plc_smooth(plc_ctx* c, const double* x, double* y, double radius) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  PLC_TRY(need_field(c, x, "x", true));
+  PLC_TRY(need_field(c, y, "y", true));
+  if (!(radius >= 0.0) || !std::isfinite(radius))
+    return fail(c, PLC_ERR_INVALID_ARG, "radius must be finite and >= 0");
+  return guarded(c, [&]() -> plc_status {
+    ensure_work_fields(c);
+    plc::gaussian_smooth(c, x, y, radius, static_cast<double*>(c->wf[12]));
+    return PLC_OK;
+  });
+}
+
+plc_status plc_log_stats(plc_ctx* c, const double* delta, double lo, double width, int nbins,
+                         long long* counts, long long* outside, double* moments) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  PLC_TRY(need_field(c, delta, "delta", true));
+  if (!(width > 0.0) || !std::isfinite(width) || !std::isfinite(lo))
+    return fail(c, PLC_ERR_INVALID_ARG, "bins need finite lo and width > 0");
+  if (nbins < 1 || nbins > 4096) return fail(c, PLC_ERR_INVALID_ARG, "nbins must be 1..4096");
+  if (!counts || !outside || !moments) return fail(c, PLC_ERR_INVALID_ARG, "NULL output");
+  return guarded(c, [&]() -> plc_status {
+    ensure_work_fields(c);
+    std::vector<long long> all(nbins + 3);
+    plc::log_stats(c, delta, lo, width, nbins, all.data(), moments,
+                   static_cast<unsigned long long*>(c->wf[12]));
+    for (int j = 0; j < nbins; ++j) counts[j] = all[j];
+    for (int j = 0; j < 3; ++j) outside[j] = all[nbins + j];
+    return PLC_OK;
+  });
+}
+
 plc_status plc_set_fft_schedule(plc_ctx* c, int f1, int f2) {
   if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
   bool ok = f1 == 0 && f2 == 0;

@@ -165,6 +165,16 @@ void profile_reset(plc_ctx* c, bool timing);
 void profile_release(plc_ctx* c);
 
 void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int nk);
+
+// Quality measures and matter statistics (stats.cu).  out = {sum ab, sum a^2,
+// sum b^2, sum (a-b)^2}; counts[nbins + 3] (below, above, invalid at the end)
+// through the device scratch dcounts[nbins + 3]; moments = {mean, variance,
+// skewness, excess kurtosis}; table: scratch of 3 (n/2)^2 + 1 doubles for
+// the smoothing multipliers.
+void compare_fields(plc_ctx* c, const double* a, const double* b, double out[4]);
+void log_stats(plc_ctx* c, const double* delta, double lo, double width, int nbins,
+               long long* counts, double* moments, unsigned long long* dcounts);
+void gaussian_smooth(plc_ctx* c, const double* x, double* y, double radius, double* table);
 void reset_ticket(plc_ctx* c);
 void read_scalars(plc_ctx* c);    // copies sc -> sc_host and synchronises
 

@@ -41,7 +41,8 @@ template <auto Kernel> inline void set_smem4(size_t bytes) {
 // transform arithmetic T: float (FP32 twiddles and multipliers) or ff
 // (float-float, from the FP64 tables).
 template <typename T, int N1, int N2, typename Pro, typename Epi, typename Fin>
-void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0) {
+void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0,
+                   const void* m_override = nullptr) {
   using Gm = Geo4<T, N1, N2>;
   using C = cpx<T>;
   constexpr bool kFF = std::is_same<T, ff>::value;
@@ -50,7 +51,9 @@ void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int
   C* A = static_cast<C*>(c->specA);
   C* B = static_cast<C*>(c->specB);
   const C* tw = kFF ? static_cast<const C*>(c->twff) : reinterpret_cast<const C*>(c->tw32);
-  const TM* M = kFF ? reinterpret_cast<const TM*>(c->M64) : reinterpret_cast<const TM*>(c->M32);
+  const TM* M = m_override ? static_cast<const TM*>(m_override)
+                           : kFF ? reinterpret_cast<const TM*>(c->M64)
+                                 : reinterpret_cast<const TM*>(c->M32);
   const dim3 gx(n / Gm::RY, n), gy(n / Gm::L, h);
   set_smem4<k4_xf<T, N1, N2, Pro>>(Gm::smem_x);
   set_smem4<k4_yf<T, N1, N2>>(Gm::smem_y);
@@ -84,17 +87,18 @@ void run_pipeline4(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int
 // Dispatch on the context's four-step schedule (every entry of kFourStep,
 // ctx.h); false when the plan has none (Stockham stages).
 template <typename T, typename Pro, typename Epi, typename Fin>
-bool run_four_step(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0) {
+bool run_four_step(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done, int s0,
+                   const void* m_override = nullptr) {
   switch (c->plan.f1 * 64 + c->plan.f2) {
-    case 16 * 64 + 16: run_pipeline4<T, 16, 16>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 16 * 64 + 12: run_pipeline4<T, 16, 12>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 12 * 64 + 16: run_pipeline4<T, 12, 16>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 16 * 64 + 8: run_pipeline4<T, 16, 8>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 8 * 64 + 16: run_pipeline4<T, 8, 16>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 12 * 64 + 8: run_pipeline4<T, 12, 8>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 8 * 64 + 12: run_pipeline4<T, 8, 12>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 8 * 64 + 8: run_pipeline4<T, 8, 8>(c, pro, epi, fin, zero_dc, done, s0); return true;
-    case 8 * 64 + 4: run_pipeline4<T, 8, 4>(c, pro, epi, fin, zero_dc, done, s0); return true;
+    case 16 * 64 + 16: run_pipeline4<T, 16, 16>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 16 * 64 + 12: run_pipeline4<T, 16, 12>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 12 * 64 + 16: run_pipeline4<T, 12, 16>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 16 * 64 + 8: run_pipeline4<T, 16, 8>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 8 * 64 + 16: run_pipeline4<T, 8, 16>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 12 * 64 + 8: run_pipeline4<T, 12, 8>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 8 * 64 + 12: run_pipeline4<T, 8, 12>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 8 * 64 + 8: run_pipeline4<T, 8, 8>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
+    case 8 * 64 + 4: run_pipeline4<T, 8, 4>(c, pro, epi, fin, zero_dc, done, s0, m_override); return true;
     default: return false;
   }
 }
@@ -102,12 +106,12 @@ bool run_four_step(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int
 // The five passes XF -> YF -> Z -> YI -> XI on the context's stream.
 template <typename T, typename Pro, typename Epi, typename Fin>
 void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done,
-                  bool gradient_sites = false) {
+                  bool gradient_sites = false, const T* m_override = nullptr) {
   using G = PassGeom<T>;
   const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
                                 : (sizeof(T) == 8 ? S_XF64 : S_XF32);
   if constexpr (sizeof(T) == 4) {
-    if (run_four_step<float>(c, pro, epi, fin, zero_dc, done, s0)) return;
+    if (run_four_step<float>(c, pro, epi, fin, zero_dc, done, s0, m_override)) return;
   }
   const int n = c->n, h = n / 2 + 1;
   const size_t sm = G::smem_bytes(c->plan);
@@ -130,7 +134,8 @@ void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int*
   }
   {
     LaunchScope ls(c, Site(s0 + 2));
-    k_z<T><<<gy, kThreads, sm, c->stream>>>(B, multiplier<T>(c), zero_dc, c->plan, tw, done);
+    k_z<T><<<gy, kThreads, sm, c->stream>>>(B, m_override ? m_override : multiplier<T>(c), zero_dc,
+                                            c->plan, tw, done);
   }
   {
     LaunchScope ls(c, Site(s0 + 3));
