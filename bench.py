@@ -566,8 +566,8 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for name, d in ests.items():
-        r, de = ctx.compare(d, d_true)
-        quality[name] = {"r": r, "d_euc": de}
+        corr, de = ctx.compare(d, d_true)
+        quality[name] = {"r": corr, "d_euc": de}
     t_cmp = (time.perf_counter() - t0) / len(ests)
     sm = torch.empty_like(d_true)
     for name, d in (("truth", d_true), ("lognormal_map", ests["lognormal_map"])):

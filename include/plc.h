@@ -120,6 +120,12 @@ typedef struct {
                           host loop reads the device scalars after each gradient,
                           CG chunk and trial.  Same iteration either way
                           (default 1). */
+  int start;           /* plc_newton_krylov_map: 1 (default) iterates from the
+                          per-cell MAP of the same posterior with the prior
+                          replaced by its diagonal (the prior variance per cell;
+                          the Lambert-W solution of Eq. MAPLNUB cell by cell),
+                          0 from s_inout itself.  ||g0|| of the stopping test is
+                          taken at s_inout either way. */
 } plc_opts;
 
 typedef struct {

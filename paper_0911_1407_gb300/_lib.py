@@ -43,7 +43,7 @@ class Opts(ctypes.Structure):
                 ("precond", ctypes.c_int), ("g0_norm", ctypes.c_double),
                 ("step_cap", ctypes.c_double), ("eta_max", ctypes.c_double),
                 ("cg_chunk", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("device_driven", ctypes.c_int)]
+                ("device_driven", ctypes.c_int), ("start", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -146,6 +146,7 @@ plc_status check_opts(plc_ctx* c, const plc_opts& o) {
   if (!(o.mixed_switch >= 0.0)) return fail(c, PLC_ERR_INVALID_ARG, "opts.mixed_switch must be >= 0");
   if (o.device_driven != 0 && o.device_driven != 1)
     return fail(c, PLC_ERR_INVALID_ARG, "opts.device_driven must be 0 or 1");
+  if (o.start != 0 && o.start != 1) return fail(c, PLC_ERR_INVALID_ARG, "opts.start must be 0 or 1");
   return PLC_OK;
 }
 
@@ -185,6 +186,7 @@ plc_status plc_default_opts(plc_opts* o) {
   o->cg_chunk = 8;
   o->mixed_switch = 1e-6;
   o->device_driven = 1;
+  o->start = 1;
   return PLC_OK;
 }
 

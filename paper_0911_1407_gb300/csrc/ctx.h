@@ -78,6 +78,7 @@ struct plc_ctx {
   double mu = 0.0;
   double inv_dc = 0.0;
   double jac_c = 0.0;          // (S^-1)_ii
+  double prior_var = 0.0;      // S_ii without the DC mode (prior variance per cell)
 
   // Reductions and device scalars.
   plc::DevScalars* sc = nullptr;
@@ -150,6 +151,10 @@ template <typename TC> void cg_update(plc_ctx* c, TC* x, TC* r, const TC* p, con
                                       const TC* D, bool jac, double rtol2, int max_iter);
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D);
 template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* dst);
+// Start point of the lognormal solve: the MAP of the same posterior with the
+// prior replaced by its diagonal (variance prior_var per cell), cell by cell.
+template <typename TS> void diag_start(plc_ctx* c, TS* s, const int32_t* N, const double* w,
+                                       double nbar);
 
 // Counts a launch and, when timing is on, brackets it with CUDA events.
 class LaunchScope {

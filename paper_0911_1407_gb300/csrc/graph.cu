@@ -96,6 +96,14 @@ __global__ void k_ctl_init(DevCtl* t, const DevScalars* sc, CtlOpts o, Handle h_
   cudaGraphSetConditional(h_newton, 1);
 }
 
+// A second FFT gradient at the start point (the first one gave g0).
+__global__ void k_ctl_restart(DevCtl* t, int nk, int fp64) {
+  t->kernels += nk;
+  t->grad_evals += 1;
+  t->grad_ffts += 1;
+  t->grad_ffts_fp64 += fp64;
+}
+
 // FP32 -> FP64 switch (PLC_MIXED): below the switch point, at the
 // tolerance, or when an FP32 step below 1e-3 failed to halve ||g||.
 __global__ void k_ctl_head(DevCtl* t, const DevScalars* sc, Handle h_switch, int nk) {
@@ -326,7 +334,7 @@ struct GraphSolve {
   DevCtl* ctl_host = nullptr;     // pinned copy
   cudaGraphExec_t exec = nullptr; // single-solve graph and its key
   const void* key_ptr[3] = {};
-  double key_val[8] = {};
+  double key_val[9] = {};
   int key_int[4] = {};
 };
 
@@ -399,6 +407,23 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
     const int nk = (int)(total_launches(c) - k0) + 1;
     k_ctl_init<<<1, 1, 0, c->stream>>>(t, c->sc, co, h_newton, nk);
     check(cudaGetLastError(), "k_ctl_init");
+    if (o.start == 1) {
+      // iterate from the per-cell diagonal-prior MAP (g0 stays at s_in)
+      const long long k1 = total_launches(c);
+      if (start64) {
+        diag_start<double>(c, s_out, N, w, nbar);
+        grad_newton<double, double, TC>(c, s_out, w, N, nbar, as<double>(f64a.y),
+                                        as<double>(f64a.g), as<TC>(f64a.D), as<TC>(f64a.r), jac);
+      } else if constexpr (kMixed) {
+        diag_start<float>(c, as<float>(f32a.s), N, w, nbar);
+        grad_newton<float, float, float>(c, as<float>(f32a.s), w, N, nbar, as<float>(f32a.y),
+                                         as<float>(f32a.g), as<float>(f32a.D), as<float>(f32a.r),
+                                         jac);
+      }
+      const int nk1 = (int)(total_launches(c) - k1) + 1;
+      k_ctl_restart<<<1, 1, 0, c->stream>>>(t, nk1, start64 ? 1 : 0);
+      check(cudaGetLastError(), "k_ctl_restart");
+    }
 
     cudaGraph_t nbody;
     add_conditional(c->stream, h_newton, cudaGraphCondTypeWhile, 1, &nbody);
@@ -480,7 +505,7 @@ void fill_stats(const DevCtl& h, plc_stats* st, double ms) {
 }
 
 bool same_key(const GraphSolve* g, const void* const* p, const double* v, const int* k) {
-  return g->exec && std::equal(p, p + 3, g->key_ptr) && std::equal(v, v + 8, g->key_val) &&
+  return g->exec && std::equal(p, p + 3, g->key_ptr) && std::equal(v, v + 9, g->key_val) &&
          std::equal(k, k + 4, g->key_int);
 }
 
@@ -492,9 +517,10 @@ plc_status newton_map_graph(plc_ctx* c, const int32_t* N, const double* w, doubl
   const auto t0 = std::chrono::steady_clock::now();
   GraphSolve* gs = graph_state(c);
   const void* kp[3] = {N, w, s_out};
-  const double kv[8] = {nbar, o.tol, o.g0_norm, o.step_cap, o.eta_max, o.mixed_switch, c->mu,
-                        c->jac_c};
-  const int ki[4] = {o.max_newton, o.max_cg, o.precond, c->plan.f1 * 64 + c->plan.f2};
+  const double kv[9] = {nbar, o.tol, o.g0_norm, o.step_cap, o.eta_max, o.mixed_switch, c->mu,
+                        c->jac_c, c->prior_var};
+  const int ki[4] = {o.max_newton, o.max_cg, o.precond * 2 + o.start,
+                     c->plan.f1 * 64 + c->plan.f2};
   if (!same_key(gs, kp, kv, ki)) {
     if (gs->exec) {
       cudaGraphExecDestroy(gs->exec);
@@ -512,7 +538,7 @@ plc_status newton_map_graph(plc_ctx* c, const int32_t* N, const double* w, doubl
     }
     cudaGraphDestroy(top);
     std::copy(kp, kp + 3, gs->key_ptr);
-    std::copy(kv, kv + 8, gs->key_val);
+    std::copy(kv, kv + 9, gs->key_val);
     std::copy(ki, ki + 4, gs->key_int);
   }
   check(cudaGraphLaunch(gs->exec, c->stream), "graph launch");
@@ -546,11 +572,13 @@ plc_status batch_map(BatchGraph* b, const std::vector<plc_ctx*>& cs, const int32
     key.push_back(s[i]);
   }
   std::vector<double> kv{o.tol, o.g0_norm, o.step_cap, o.eta_max, o.mixed_switch,
-                         (double)o.max_newton, (double)o.max_cg, (double)o.precond};
+                         (double)o.max_newton, (double)o.max_cg, (double)o.precond,
+                         (double)o.start};
   for (size_t i = 0; i < m; ++i) {
     kv.push_back(nbar[i]);
     kv.push_back(cs[i]->mu);
     kv.push_back(cs[i]->jac_c);
+    kv.push_back(cs[i]->prior_var);
     kv.push_back((double)(cs[i]->plan.f1 * 64 + cs[i]->plan.f2));
   }
   if (!b->exec || key != b->key || kv != b->key_val) {

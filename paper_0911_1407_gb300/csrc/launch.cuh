@@ -274,6 +274,14 @@ void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, 
   check(cudaGetLastError(), "k_newton_update");
 }
 
+template <typename TS> void diag_start(plc_ctx* c, TS* s, const int32_t* N, const double* w,
+                                       double nbar) {
+  LaunchScope ls(c, S_SETUP);
+  k_diag_start<TS><<<pw_blocks(c), kThreads, 0, c->stream>>>(
+      s, N, w, (float)nbar, (float)c->mu, (float)c->prior_var, c->n3());
+  check(cudaGetLastError(), "k_diag_start");
+}
+
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D) {
   LaunchScope ls(c, S_DIAG);
   k_diag<TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(s, w, nbar, D, c->n3());

@@ -677,6 +677,42 @@ k_diag(const double* __restrict__ s, const double* __restrict__ w, double nbar,
     D[i] = (TC)(nbar * (w ? w[i] : 1.0) * exp(s[i]));
 }
 
+// Lambert W of x = e^L from L = ln x (x up to e^300 and beyond), in FP32:
+// Newton's method on w + ln w = L, the defining equation w e^w = x in log
+// form, from w = x / (1 + x) (L < 1) or w = L - ln L (L >= 1); four steps
+// reach FP32 accuracy.  L = -inf gives 0.
+__device__ __forceinline__ float lambert_w_log(float L) {
+  if (L == -INFINITY) return 0.f;
+  float w;
+  if (L < 1.f) {
+    const float x = __expf(L);
+    w = x / (1.f + x);
+  } else {
+    w = L - __logf(L);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) w = w * (1.f + L - __logf(w)) / (1.f + w);
+  return w;
+}
+
+// Per cell, the MAP of -ln P with S replaced by sigma2 I (Eq. MAPLNUB cell by
+// cell): (s - mu) / sigma2 + nbar w e^s = N, s = mu + sigma2 N - W(x),
+// x = sigma2 w nbar e^{mu + sigma2 N}.  A start point for the solve: the
+// per-cell balance of prior and counts without the prior's correlations.
+template <typename TS>
+__global__ void __launch_bounds__(kThreads)
+k_diag_start(TS* __restrict__ s, const int32_t* __restrict__ N, const double* __restrict__ w,
+             float nbar, float mu, float sigma2, size_t n3) {
+  const float lw0 = __logf(sigma2 * nbar);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float a = mu + sigma2 * (float)N[i];
+    const float wi = w ? (float)w[i] : 1.f;
+    const float L = wi > 0.f ? lw0 + __logf(wi) + a : -INFINITY;
+    s[i] = (TS)(a - lambert_w_log(L));
+  }
+}
+
 template <typename TD, typename TS>
 __global__ void __launch_bounds__(kThreads)
 k_convert(const TS* __restrict__ src, TD* __restrict__ dst, size_t n3) {

@@ -34,18 +34,24 @@ __global__ void k_build_multiplier(double* __restrict__ M64, float* __restrict__
   }
 }
 
-// (S^-1)_ii = n^-3 sum_k 1/lambda_k = sum over all n^3 modes of M[|m|^2].
+// (S^-1)_ii = n^-3 sum_k 1/lambda_k = sum over all n^3 modes of M[|m|^2],
+// and the prior variance per cell without the DC mode,
+// S_ii = n^-3 sum_{k != 0} lambda_k = n^-6 sum_{k != 0} 1 / M[|m|^2].
 __global__ void __launch_bounds__(kThreads)
 k_jacobi_constant(const double* __restrict__ M64, int n, RedArgs ra) {
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   const size_t n3 = (size_t)n * n * n;
+  const double inv_n6 = 1.0 / ((double)n3 * (double)n3);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
        i += (size_t)gridDim.x * blockDim.x) {
     const int kx = (int)(i % n), ky = (int)((i / n) % n), kz = (int)(i / ((size_t)n * n));
     const int mx = min(kx, n - kx), my = min(ky, n - ky), mz = min(kz, n - kz);
-    acc[0] += M64[mx * mx + my * my + mz * mz];
+    const int m2 = mx * mx + my * my + mz * mz;
+    const double v = M64[m2];
+    acc[0] += v;
+    if (m2 > 0 && v > 0.0) acc[1] += inv_n6 / v;
   }
-  block_reduce_finish<1, 0u>(acc, ra, FinStore<1>{});
+  block_reduce_finish<2, 0u>(acc, ra, FinStore<2>{});
 }
 
 const char* const kSiteNames[S_NSITES] = {
@@ -133,6 +139,7 @@ void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int n
   check(cudaGetLastError(), "k_jacobi_constant");
   read_scalars(c);
   c->jac_c = c->sc_host->red[0];
+  c->prior_var = c->sc_host->red[1];
 }
 
 }  // namespace plc

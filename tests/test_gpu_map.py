@@ -160,3 +160,21 @@ def test_map_mixed_to_fp64_accuracy(plc, key):
     assert st["grad_rel"] < 1e-10 and st["grad_ffts_fp64"] >= 1
     err = np.abs(s - ref.s) / np.maximum(np.abs(ref.s), 1.0)
     assert err.max() <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_map_start_point_option(plc, precision):
+    """The diagonal-prior start (opts.start = 1) reaches the same MAP as the
+    start at mu with fewer Newton steps; ||g0|| is taken at mu in both."""
+    m = mocks.make_mock(mocks.WORKLOADS["adjoint128"])
+    c = plc.Context(m.n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    Nd = dev(m.N, torch.int32)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    r0 = c.newton_krylov_map(Nd, None, m.nbar, tol=tol, start=0)
+    r1 = c.newton_krylov_map(Nd, None, m.nbar, tol=tol, start=1)
+    assert r0.stats["g0_norm"] == r1.stats["g0_norm"]
+    assert r1.stats["newton_iters"] < r0.stats["newton_iters"]
+    assert r1.stats["grad_ffts"] == r0.stats["grad_ffts"] + 1
+    bar = 1e-8 if precision == "fp64" else 1e-4
+    assert np.max(np.abs(host(r0.s) - host(r1.s))) <= bar
