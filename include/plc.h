@@ -191,6 +191,54 @@ plc_status plc_gauss_map(plc_ctx* ctx, const int32_t* N, const void* w, double n
 plc_status plc_wiener_lsq(plc_ctx* ctx, const int32_t* N, const void* w, double nbar,
                           double* delta_out, const plc_opts* opts, plc_stats* stats);
 
+/* Linear bias of the galaxy field (Sec. 2.4.1, with Sec. 2.2.1): the
+ * expected counts become nbar w (1 + B delta_M), B the convolution whose
+ * Fourier multiplier is the bias b(|k|) (b = sqrt(P_g / P_M) for the galaxy
+ * and matter spectra).  k, b: HOST arrays of nb >= 2 points, k > 0 strictly
+ * ascending, b > 0, covering [2 pi / L, sqrt(3) pi n / L] like the P(k)
+ * table of plc_set_prior; b is linear in (ln k, ln b) between table points.
+ * b_dc > 0: the multiplier of the DC mode.  Replaces an earlier table; the
+ * context copies what it needs.  Synchronises the stream. */
+plc_status plc_set_bias(plc_ctx* ctx, const double* k, const double* b, int nb, double b_dc);
+
+/* -ln P of the lognormal-prior Poisson model with linear bias (Sec. 2.4.1)
+ * at s = ln(1 + delta_M):
+ *   L(s) = 1/2 (s - mu)^T S^-1 (s - mu) + sum_i [ nbar w_i u_i - N_i ln u_i ],
+ *   u = 1 + B(e^s - 1),
+ * +inf where u_i <= 0 in a cell with N_i > 0, and its gradient (the MAP
+ * equation of Sec. 2.4.1)
+ *   g = S^-1 (s - mu) + e^s . B(nbar w - N / u).
+ * Needs plc_set_prior and plc_set_bias.  s, grad: fields of the context's
+ * precision (grad may be NULL); N: int32 field; w: double field or NULL;
+ * neg_logpost: host double or NULL (PLC_ERR_NONFINITE when it is not
+ * finite).  Synchronises the stream when neg_logpost is given. */
+plc_status plc_bias_logpost_grad(plc_ctx* ctx, const void* s, const int32_t* N, const void* w,
+                                 double nbar, double* neg_logpost, void* grad);
+
+/* The exact Hessian of that L applied to v:
+ *   H v = S^-1 v + d1 . v + e^s . B((N / u^2) . B(e^s . v)),
+ *   d1 = e^s . B(nbar w - N / u).
+ * H need not be positive definite.  s, v, Hv: fields of the context's
+ * precision; N: int32 field; w: double field or NULL. */
+plc_status plc_bias_hessvec(plc_ctx* ctx, const void* s, const int32_t* N, const void* w,
+                            double nbar, const void* v, void* Hv);
+
+/* MAP of that L: the inexact Newton-Krylov iteration of
+ * plc_newton_krylov_map (host-driven; opts->device_driven and opts->start are
+ * not used) with the exact Hessian above.  The CG stops at non-positive
+ * curvature and keeps its iterate (the preconditioned gradient step when
+ * that happens on its first direction); tau = 1 when xi^T H xi <= 0; trial
+ * points outside the domain count as L = +inf and are halved.  The prior
+ * term is carried forward with S^-1 xi, one FFT pipeline per Newton step.
+ * s_inout (double, device): start point on entry (0, i.e. delta_M = 0, is
+ * inside the domain for any b), MAP on exit.  PLC_MIXED: FP32 state and CG
+ * until max(mixed_switch, tol) or FP32 stagnation, then FP64 state (FP64
+ * transforms) with the FP32 CG; the stop test is passed on an FP64 gradient.
+ * Returns PLC_ERR_NONFINITE when the start point is outside the domain.
+ * Synchronises the stream. */
+plc_status plc_bias_map(plc_ctx* ctx, const int32_t* N, const void* w, double nbar,
+                        double* s_inout, const plc_opts* opts, plc_stats* stats);
+
 /* Implicit adjoint of the MAP (implicit-function theorem on g(s*) = 0; the
  * paper has no counterpart).  For a cotangent u (double field), solves
  * H lam = u by CG at s_map and returns

@@ -25,7 +25,8 @@ STATUS = {0: "PLC_OK", 1: "PLC_ERR_INVALID_ARG", 2: "PLC_ERR_CUDA", 3: "PLC_ERR_
 # Every symbol include/plc.h declares.
 EXPORTS = ["plc_create", "plc_destroy", "plc_set_prior", "plc_prior_apply", "plc_logpost_grad",
            "plc_hessvec", "plc_default_opts", "plc_newton_krylov_map", "plc_map_vjp",
-           "plc_gauss_map", "plc_wiener_lsq", "plc_compare", "plc_smooth", "plc_log_stats",
+           "plc_gauss_map", "plc_wiener_lsq", "plc_set_bias", "plc_bias_logpost_grad",
+           "plc_bias_hessvec", "plc_bias_map", "plc_compare", "plc_smooth", "plc_log_stats",
            "plc_set_fft_schedule", "plc_autotune",
            "plc_batch_create", "plc_batch_map", "plc_batch_destroy",
            "plc_profile_enable", "plc_profile_read", "plc_hessvec_noalloc", "plc_last_error",
@@ -88,6 +89,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "plc_map_vjp": (I, [P, P, P, D, P, P, DP, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_wiener_lsq": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_gauss_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+        "plc_set_bias": (I, [P, DP, DP, I, D]),
+        "plc_bias_logpost_grad": (I, [P, P, P, P, D, DP, P]),
+        "plc_bias_hessvec": (I, [P, P, P, P, D, P, P]),
+        "plc_bias_map": (I, [P, P, P, D, P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
         "plc_compare": (I, [P, P, P, DP, DP]),
         "plc_smooth": (I, [P, P, P, D]),
         "plc_log_stats": (I, [P, P, D, D, I, ctypes.POINTER(ctypes.c_longlong),
@@ -282,6 +287,51 @@ class Context:
         if raise_on_fail:
             self._check(st)
         return out, st, stt.as_dict()
+
+    # -- linear bias (Sec. 2.4.1) -------------------------------------------
+    def set_bias(self, k, b, b_dc: float = 1.0):
+        """Bias table b(k) (linear in ln k, ln b) and the DC multiplier."""
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        DP = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.plc_set_bias(self._h, k.ctypes.data_as(DP), b.ctypes.data_as(DP),
+                                          int(k.size), float(b_dc)))
+
+    def bias_logpost_grad(self, s, N, w, nbar: float, grad: Optional[torch.Tensor] = None,
+                          want_grad: bool = True):
+        """-ln P and its gradient with linear bias; s, grad in the context's
+        precision, w float64 (or None)."""
+        if want_grad and grad is None:
+            grad = self.field()
+        f = ctypes.c_double()
+        self._check(self.lib.plc_bias_logpost_grad(
+            self._h, _ptr(s, self.n, self.real, "s"), _ptr(N, self.n, torch.int32, "N"),
+            _ptr(w, self.n, torch.float64, "w", False), float(nbar), ctypes.byref(f),
+            _ptr(grad, self.n, self.real, "grad", False)))
+        return f.value, grad
+
+    def bias_hessvec(self, s, N, w, nbar: float, v, out: Optional[torch.Tensor] = None):
+        """Exact Hessian of the linear-bias -ln P at s applied to v."""
+        out = self.field() if out is None else out
+        self._check(self.lib.plc_bias_hessvec(
+            self._h, _ptr(s, self.n, self.real, "s"), _ptr(N, self.n, torch.int32, "N"),
+            _ptr(w, self.n, torch.float64, "w", False), float(nbar),
+            _ptr(v, self.n, self.real, "v"), _ptr(out, self.n, self.real, "Hv")))
+        return out
+
+    def bias_map(self, N, w, nbar: float, s: Optional[torch.Tensor] = None,
+                 raise_on_fail: bool = True, **opts) -> MapResult:
+        """MAP with linear bias; s (float64) is the start point (default 0,
+        delta_M = 0) and is overwritten."""
+        if s is None:
+            s = torch.zeros((self.n,) * 3, dtype=torch.float64, device="cuda")
+        o, stt = default_opts(**opts), Stats()
+        st = self.lib.plc_bias_map(
+            self._h, _ptr(N, self.n, torch.int32, "N"), _ptr(w, self.n, torch.float64, "w", False),
+            float(nbar), _ptr(s, self.n, torch.float64, "s"), ctypes.byref(o), ctypes.byref(stt))
+        if raise_on_fail:
+            self._check(st)
+        return MapResult(s, st, stt.as_dict())
 
     def compare(self, a, b):
         """(r, D_Euc) of two float64 fields."""

@@ -13,6 +13,7 @@
 
 #include "ctx.h"
 #include "graph.h"
+#include "bias.h"
 #include "solver.h"
 
 namespace {
@@ -87,10 +88,12 @@ void release(plc_ctx* c) {
   plc::graph_release(c);
   plc::profile_release(c);
   void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->twff, c->expff, c->M64, c->M32,
-                  c->lk, c->lP, c->sc, c->partials};
+                  c->lk, c->lP, c->sc, c->partials, c->Mb64, c->Mb32, c->lkb, c->lbb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->wf)
+    if (p) cudaFree(p);
+  for (void* p : c->bwf)
     if (p) cudaFree(p);
   if (c->sc_host) cudaFreeHost(c->sc_host);
 }
@@ -98,6 +101,13 @@ void release(plc_ctx* c) {
 void ensure_work_fields(plc_ctx* c) {
   const size_t b = sizeof(double) * c->n3();
   for (void*& p : c->wf)
+    if (!p) dalloc(&p, b);
+}
+
+void ensure_bias_fields(plc_ctx* c) {
+  ensure_work_fields(c);
+  const size_t b = sizeof(double) * c->n3();
+  for (void*& p : c->bwf)
     if (!p) dalloc(&p, b);
 }
 
@@ -445,6 +455,155 @@ plc_status plc_wiener_lsq(plc_ctx* c, const int32_t* N, const void* w, double nb
                               : plc::wiener_lsq<float>(c, N, wd, nbar, delta_out, o, stats);
     if (st == PLC_ERR_NOT_CONVERGED) fail(c, st, "CG did not reach the tolerance");
     else if (st == PLC_ERR_CG_BREAKDOWN) fail(c, st, "CG breakdown on the first step");
+    else c->err.clear();
+    return st;
+  });
+}
+
+// ------------------------------ linear bias --------------------------------
+
+plc_status plc_set_bias(plc_ctx* c, const double* k, const double* b, int nb, double b_dc) {
+  if (!c) return fail(nullptr, PLC_ERR_INVALID_ARG, "null context");
+  if (!k || !b || nb < 2) return fail(c, PLC_ERR_INVALID_ARG, "need k, b arrays with nb >= 2");
+  for (int i = 0; i < nb; ++i) {
+    if (!(k[i] > 0.0) || !std::isfinite(k[i]) || !(b[i] > 0.0) || !std::isfinite(b[i]))
+      return fail(c, PLC_ERR_INVALID_ARG, "k and b must be finite and > 0");
+    if (i && !(k[i] > k[i - 1])) return fail(c, PLC_ERR_INVALID_ARG, "k must be strictly ascending");
+  }
+  const double kf = 2.0 * M_PI / c->box;
+  const double kmax = std::sqrt(3.0) * M_PI * c->n / c->box;
+  if (k[0] > kf * (1.0 + 1e-12) || k[nb - 1] < kmax * (1.0 - 1e-12))
+    return fail(c, PLC_ERR_INVALID_ARG, "b(k) table must cover [2 pi / L, sqrt(3) pi n / L]");
+  if (!(b_dc > 0.0) || !std::isfinite(b_dc))
+    return fail(c, PLC_ERR_INVALID_ARG, "b_dc must be finite and > 0");
+  return guarded(c, [&]() -> plc_status {
+    const int half = c->n / 2;
+    const int nm2 = 3 * half * half + 1;
+    if (!c->Mb64) {
+      dalloc(&c->Mb64, sizeof(double) * nm2);
+      dalloc(&c->Mb32, sizeof(float) * nm2);
+    }
+    if (c->nb_cap < nb) {
+      if (c->lkb) cudaFree(c->lkb);
+      if (c->lbb) cudaFree(c->lbb);
+      c->lkb = nullptr;
+      c->lbb = nullptr;
+      dalloc(&c->lkb, sizeof(double) * nb);
+      dalloc(&c->lbb, sizeof(double) * nb);
+      c->nb_cap = nb;
+    }
+    std::vector<double> lk(nb), lb(nb);
+    for (int i = 0; i < nb; ++i) {
+      lk[i] = std::log(k[i]);
+      lb[i] = std::log(b[i]);
+    }
+    c->have_bias = false;
+    plc::build_bias(c, lk.data(), lb.data(), nb, b_dc);
+    c->have_bias = true;
+    c->err.clear();
+    return PLC_OK;
+  });
+}
+
+static plc_status need_bias(plc_ctx* c) {
+  PLC_TRY(need_prior(c));
+  if (!c->have_bias) return fail(c, PLC_ERR_INVALID_ARG, "no bias table: call plc_set_bias first");
+  return PLC_OK;
+}
+
+// y, q, Q at s (work fields of the bias solve) and the gradient; E, d1 on
+// request.  T: the context's field type.
+extern "C++" template <typename T>
+void bias_point(plc_ctx* c, const T* s, const int32_t* N, const double* w, double nbar,
+                T* grad, bool hess) {
+  T* y = static_cast<T*>(c->bwf[2]);
+  T* q = static_cast<T*>(c->bwf[4]);
+  T* E = static_cast<T*>(c->bwf[6]);
+  T* Q = static_cast<T*>(c->bwf[7]);
+  T* d1 = static_cast<T*>(c->bwf[8]);
+  plc::reset_ticket(c);
+  plc::bias_prior<T, T>(c, s, c->mu, y);
+  plc::bias_density<T, T>(c, s, nullptr, 0.0, nullptr, y, nullptr, nullptr, N, w, nbar, q, Q);
+  plc::bias_gradient<T, T>(c, s, y, q, Q, grad, nullptr, hess ? E : nullptr, hess ? d1 : nullptr,
+                           nullptr, false);
+}
+
+plc_status plc_bias_logpost_grad(plc_ctx* c, const void* s, const int32_t* N, const void* w,
+                                 double nbar, double* neg_logpost, void* grad) {
+  PLC_TRY(need_bias(c));
+  PLC_TRY(need_field(c, s, "s", true));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, grad, "grad", false));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  return guarded(c, [&]() -> plc_status {
+    ensure_bias_fields(c);
+    const double* wd = static_cast<const double*>(w);
+    if (c->precision == PLC_FP64)
+      bias_point<double>(c, static_cast<const double*>(s), N, wd, nbar, static_cast<double*>(grad),
+                         false);
+    else
+      bias_point<float>(c, static_cast<const float*>(s), N, wd, nbar, static_cast<float*>(grad),
+                        false);
+    if (neg_logpost) {
+      plc::read_scalars(c);
+      const double* r = c->sc_host->red;
+      *neg_logpost = 0.5 * r[0] + r[1];
+      if (!std::isfinite(*neg_logpost))
+        return fail(c, PLC_ERR_NONFINITE, "non-finite -ln P (u <= 0 where N > 0?)");
+    }
+    return PLC_OK;
+  });
+}
+
+plc_status plc_bias_hessvec(plc_ctx* c, const void* s, const int32_t* N, const void* w,
+                            double nbar, const void* v, void* Hv) {
+  PLC_TRY(need_bias(c));
+  PLC_TRY(need_field(c, s, "s", true));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, v, "v", true));
+  PLC_TRY(need_field(c, Hv, "Hv", true));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  return guarded(c, [&]() -> plc_status {
+    ensure_bias_fields(c);
+    const double* wd = static_cast<const double*>(w);
+    void** B = c->bwf;
+    if (c->precision == PLC_FP64) {
+      using T = double;
+      bias_point<T>(c, static_cast<const T*>(s), N, wd, nbar, nullptr, true);
+      plc::bias_hv<T>(c, static_cast<const T*>(v), static_cast<T*>(B[6]), static_cast<T*>(B[7]),
+                      static_cast<T*>(B[8]), static_cast<T*>(B[10]), static_cast<T*>(B[11]),
+                      static_cast<T*>(Hv));
+    } else {
+      using T = float;
+      bias_point<T>(c, static_cast<const T*>(s), N, wd, nbar, nullptr, true);
+      plc::bias_hv<T>(c, static_cast<const T*>(v), static_cast<T*>(B[6]), static_cast<T*>(B[7]),
+                      static_cast<T*>(B[8]), static_cast<T*>(B[10]), static_cast<T*>(B[11]),
+                      static_cast<T*>(Hv));
+    }
+    return PLC_OK;
+  });
+}
+
+plc_status plc_bias_map(plc_ctx* c, const int32_t* N, const void* w, double nbar,
+                        double* s_inout, const plc_opts* opts, plc_stats* stats) {
+  PLC_TRY(need_bias(c));
+  PLC_TRY(need_field(c, N, "N", true));
+  PLC_TRY(need_field(c, w, "w", false));
+  PLC_TRY(need_field(c, s_inout, "s_inout", true));
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return fail(c, PLC_ERR_INVALID_ARG, "nbar must be > 0");
+  const plc_opts o = resolve_opts(opts);
+  PLC_TRY(check_opts(c, o));
+  return guarded(c, [&]() -> plc_status {
+    ensure_bias_fields(c);
+    const double* wd = static_cast<const double*>(w);
+    const plc_status st = c->precision == PLC_FP64
+                              ? plc::bias_map<double>(c, N, wd, nbar, s_inout, o, stats)
+                              : plc::bias_map<float>(c, N, wd, nbar, s_inout, o, stats);
+    if (st == PLC_ERR_NOT_CONVERGED) fail(c, st, "Newton iteration cap reached");
+    else if (st == PLC_ERR_NONFINITE)
+      fail(c, st, "non-finite gradient or objective (start point outside u > 0?)");
     else c->err.clear();
     return st;
   });

@@ -25,6 +25,10 @@ enum Site {
   S_GXFF, S_GYFF, S_GZFF, S_GYIFF, S_GXIFF,
   S_CG_INIT, S_CG_UPDATE64, S_CG_UPDATE32, S_NEWTON_UPDATE64, S_NEWTON_UPDATE32,
   S_DIAG, S_CONVERT, S_SETUP, S_BOUNDARY,
+  // pipelines and element-wise kernels of the linear-bias model
+  S_BXF64, S_BYF64, S_BZ64, S_BYI64, S_BXI64,
+  S_BXF32, S_BYF32, S_BZ32, S_BYI32, S_BXI32,
+  S_BIAS,
   S_NSITES
 };
 extern const char* const kSiteNames[S_NSITES];
@@ -80,6 +84,15 @@ struct plc_ctx {
   double jac_c = 0.0;          // (S^-1)_ii
   double prior_var = 0.0;      // S_ii without the DC mode (prior variance per cell)
 
+  // Linear bias (Sec. 2.4.1): b(|k|) / n^3 per |m|^2, FP64 and FP32 copies,
+  // and the ln-tables it was built from.
+  double* Mb64 = nullptr;
+  float* Mb32 = nullptr;
+  double* lkb = nullptr;
+  double* lbb = nullptr;
+  int nb_cap = 0;
+  bool have_bias = false;
+
   // Reductions and device scalars.
   plc::DevScalars* sc = nullptr;
   plc::DevScalars* sc_host = nullptr;   // pinned
@@ -89,6 +102,9 @@ struct plc_ctx {
   // Solver work fields, each n^3 doubles, allocated on first use.
   static constexpr int kNumWork = 13;
   void* wf[kNumWork] = {};
+  // Extra work fields of the linear-bias solve, allocated on its first use.
+  static constexpr int kNumBiasWork = 12;
+  void* bwf[kNumBiasWork] = {};
 
   plc::Profiler prof;
   std::string err;
@@ -170,6 +186,8 @@ void profile_reset(plc_ctx* c, bool timing);
 void profile_release(plc_ctx* c);
 
 void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int nk);
+// Bias multipliers b(|k|) / n^3 from ln k, ln b tables (b_dc for the DC mode).
+void build_bias(plc_ctx* c, const double* lk_host, const double* lb_host, int nb, double b_dc);
 
 // Quality measures and matter statistics (stats.cu).  out = {sum ab, sum a^2,
 // sum b^2, sum (a-b)^2}; counts[nbins + 3] (below, above, invalid at the end)

@@ -106,10 +106,14 @@ bool run_four_step(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int
 // The five passes XF -> YF -> Z -> YI -> XI on the context's stream.
 template <typename T, typename Pro, typename Epi, typename Fin>
 void run_pipeline(plc_ctx* c, Pro pro, Epi epi, Fin fin, int zero_dc, const int* done,
-                  bool gradient_sites = false, const T* m_override = nullptr) {
+                  int sites = 0, const T* m_override = nullptr) {
   using G = PassGeom<T>;
-  const int s0 = gradient_sites ? (sizeof(T) == 8 ? S_GXF64 : S_GXF32)
-                                : (sizeof(T) == 8 ? S_XF64 : S_XF32);
+  // site group: 0 the Hessian-vector product and public operators, 1 the
+  // Newton gradient, 2 the linear-bias model
+  constexpr bool k64 = sizeof(T) == 8;
+  const int s0 = sites == 2   ? (k64 ? S_BXF64 : S_BXF32)
+                 : sites == 1 ? (k64 ? S_GXF64 : S_GXF32)
+                              : (k64 ? S_XF64 : S_XF32);
   if constexpr (sizeof(T) == 4) {
     if (run_four_step<float>(c, pro, epi, fin, zero_dc, done, s0, m_override)) return;
   }

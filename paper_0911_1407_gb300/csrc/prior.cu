@@ -6,6 +6,20 @@
 namespace plc {
 
 // ----------------------------- prior set-up -------------------------------
+// ln f(|k|) at |k| = (2 pi / L) sqrt(m2), m2 > 0, for a table linear in
+// (ln k, ln f) between the points lk = ln k, lf = ln f.
+__device__ double interp_ln(int m2, double box, const double* __restrict__ lk,
+                            const double* __restrict__ lf, int nk) {
+  const double lnk = log(2.0 * 3.14159265358979323846 / box) + 0.5 * log((double)m2);
+  int lo = 0, hi = nk - 1;                 // largest j with lk[j] <= lnk
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (lk[mid] <= lnk) lo = mid; else hi = mid;
+  }
+  const double t = (lnk - lk[lo]) / (lk[lo + 1] - lk[lo]);
+  return lf[lo] + t * (lf[lo + 1] - lf[lo]);
+}
+
 // M[m2] = 1 / (lambda n^3) for |m|^2 = m2, lambda = P(|k|) n^3 / L^3 with
 // |k| = (2 pi / L) sqrt(m2) and P linear in (ln k, ln P) between the table
 // points lk = ln k, lP = ln P.  M[0] = inv_lambda_dc / n^3.
@@ -18,17 +32,22 @@ __global__ void k_build_multiplier(double* __restrict__ M64, float* __restrict__
     if (m2 == 0) {
       v = inv_dc / n3;
     } else {
-      const double lnk = log(2.0 * 3.14159265358979323846 / box) + 0.5 * log((double)m2);
-      int lo = 0, hi = nk - 1;                 // largest j with lk[j] <= lnk
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (lk[mid] <= lnk) lo = mid; else hi = mid;
-      }
-      const double t = (lnk - lk[lo]) / (lk[lo + 1] - lk[lo]);
-      const double lnP = lP[lo] + t * (lP[lo + 1] - lP[lo]);
-      const double lam = exp(lnP) * n3 / (box * box * box);
+      const double lam = exp(interp_ln(m2, box, lk, lP, nk)) * n3 / (box * box * box);
       v = 1.0 / (lam * n3);
     }
+    M64[m2] = v;
+    M32[m2] = (float)v;
+  }
+}
+
+// The bias convolution B of Sec. 2.4.1: Mb[m2] = b(|k|) / n^3 (the inverse
+// transform is unnormalised), b linear in (ln k, ln b); Mb[0] = b_dc / n^3.
+__global__ void k_build_bias(double* __restrict__ M64, float* __restrict__ M32, int nm2, int n,
+                             double box, const double* __restrict__ lk,
+                             const double* __restrict__ lb, int nk, double b_dc) {
+  const double n3 = (double)n * n * n;
+  for (int m2 = blockIdx.x * blockDim.x + threadIdx.x; m2 < nm2; m2 += gridDim.x * blockDim.x) {
+    const double v = (m2 == 0 ? b_dc : exp(interp_ln(m2, box, lk, lb, nk))) / n3;
     M64[m2] = v;
     M32[m2] = (float)v;
   }
@@ -61,7 +80,10 @@ const char* const kSiteNames[S_NSITES] = {
     "grad_xf_f32", "grad_yf_f32", "grad_z_f32", "grad_yi_f32", "grad_xi_f32",
     "grad_xf_ff", "grad_yf_ff", "grad_z_ff", "grad_yi_ff", "grad_xi_ff",
     "cg_init", "cg_update_f64", "cg_update_f32", "newton_update_f64", "newton_update_f32",
-    "diag", "convert", "setup", "boundary"};
+    "diag", "convert", "setup", "boundary",
+    "bias_xf_f64", "bias_yf_f64", "bias_z_f64", "bias_yi_f64", "bias_xi_f64",
+    "bias_xf_f32", "bias_yf_f32", "bias_z_f32", "bias_yi_f32", "bias_xi_f32",
+    "bias_misc"};
 
 constexpr int kProfSlots = 512;
 
@@ -140,6 +162,20 @@ void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int n
   read_scalars(c);
   c->jac_c = c->sc_host->red[0];
   c->prior_var = c->sc_host->red[1];
+}
+
+void build_bias(plc_ctx* c, const double* lk_host, const double* lb_host, int nb, double b_dc) {
+  check(cudaMemcpyAsync(c->lkb, lk_host, sizeof(double) * nb, cudaMemcpyHostToDevice, c->stream),
+        "copy ln k");
+  check(cudaMemcpyAsync(c->lbb, lb_host, sizeof(double) * nb, cudaMemcpyHostToDevice, c->stream),
+        "copy ln b");
+  const int nm2 = 3 * (c->n / 2) * (c->n / 2) + 1;
+  const int nblk = (nm2 + kThreads - 1) / kThreads;
+  LaunchScope ls(c, S_SETUP);
+  k_build_bias<<<nblk, kThreads, 0, c->stream>>>(c->Mb64, c->Mb32, nm2, c->n, c->box, c->lkb,
+                                                 c->lbb, nb, b_dc);
+  check(cudaGetLastError(), "k_build_bias");
+  check(cudaStreamSynchronize(c->stream), "stream synchronize");
 }
 
 }  // namespace plc

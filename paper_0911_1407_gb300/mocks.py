@@ -313,6 +313,16 @@ def batch_specs(seed_base: int = 1):
     return specs
 
 
+def bias_table(n: int, box: float, b0: float = 1.5, tilt: float = 0.1, k_ref: float = 0.1,
+               nb: int = 32):
+    """A scale-dependent linear bias table covering an n^3 grid of side `box`:
+    b(k) = b0 (k / k_ref)^tilt (k in h/Mpc), the galaxy-to-matter amplitude
+    ratio sqrt(P_g / P_M) of a mildly scale-dependent tracer."""
+    kf = 2 * math.pi / box
+    k = np.exp(np.linspace(math.log(0.5 * kf), math.log(1.02 * math.sqrt(3) * math.pi * n / box), nb))
+    return k, b0 * (k / k_ref) ** tilt
+
+
 def small_spec(n: int, box: float = 200.0, sigma_G: float = 1.0,
                nbar: float = 2.0, selection: str = "uniform", seed: int = 1,
                nbins: int = 512) -> MockSpec:
@@ -330,5 +340,5 @@ __all__ = [
     "philox4x32_10", "uniform_pair", "white_noise", "pk_shape",
     "amplitude_for_sigma", "pk_table", "gaussian_field", "poisson_counts",
     "radial_masked_selection", "MockSpec", "Mock", "WORKLOADS", "make_mock",
-    "batch_specs", "small_spec", "digest", "replace",
+    "batch_specs", "small_spec", "bias_table", "digest", "replace",
 ]

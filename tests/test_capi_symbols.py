@@ -74,3 +74,19 @@ def test_batch_validation_without_gpu(lib):
     assert lib.plc_batch_map(None, None, None, None, None, None, None, None) == 1
     lib.plc_batch_destroy.argtypes = [P]
     assert lib.plc_batch_destroy(None) == 0
+
+
+def test_bias_validation_without_gpu(lib):
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    DP = ctypes.POINTER(D)
+    lib.plc_set_bias.argtypes = [P, DP, DP, ctypes.c_int, D]
+    k = (D * 2)(0.1, 1.0)
+    b = (D * 2)(1.2, 1.5)
+    assert lib.plc_set_bias(None, k, b, 2, 1.0) == 1
+    lib.plc_bias_map.argtypes = [P] * 3 + [D] + [P] * 3
+    assert lib.plc_bias_map(None, None, None, 1.0, None, None, None) == 1
+    lib.plc_bias_logpost_grad.argtypes = [P] * 4 + [D, P, P]
+    assert lib.plc_bias_logpost_grad(None, None, None, None, 1.0, None, None) == 1
+    lib.plc_bias_hessvec.argtypes = [P] * 4 + [D, P, P]
+    assert lib.plc_bias_hessvec(None, None, None, None, 1.0, None, None) == 1
