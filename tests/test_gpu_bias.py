@@ -44,13 +44,15 @@ def _bp(m, kb, b, b_dc):
     return ob.BiasProblem(_problem(m), ob.bias_multipliers(m.n, m.box, kb, b, b_dc))
 
 
-def _point(m, seed, amp=0.3):
+def _point(m, seed, amp=0.1):
+    """A point inside the domain u > 0 for the tables used here (white noise
+    of small amplitude around delta_M = 0)."""
     rng = np.random.default_rng(seed)
-    return m.mu + amp * rng.standard_normal((m.n,) * 3)
+    return amp * rng.standard_normal((m.n,) * 3)
 
 
 @pytest.mark.parametrize("n,sel,b0,tilt", [(24, "radial_masked", 1.4, 0.1), (18, "uniform", 0.8, -0.2),
-                                           (32, "uniform", 1.6, 0.3)])
+                                           (32, "uniform", 1.6, 0.15)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_operators_match_oracle(plc, n, sel, b0, tilt, precision):
     m = small_mock(n, sel, sigma=1.0, nbar=1.5)
@@ -59,6 +61,7 @@ def test_operators_match_oracle(plc, n, sel, b0, tilt, precision):
     s = _point(m, n)
     v = np.random.default_rng(n + 1).standard_normal(s.shape)
     f_ref = ob.bias_neg_log_posterior(s, q)
+    assert math.isfinite(f_ref)
     g_ref = ob.bias_gradient(s, q)
     h_ref = ob.bias_hessvec(s, v, q)
     c = _ctx(plc, m, precision, kb, b, b0)
@@ -175,6 +178,18 @@ def test_bias_production256_is_a_map_for_the_oracle(plc):
     assert rel < 1e-6
     assert abs(rel - r.stats["grad_rel"]) <= 1e-3 * r.stats["grad_rel"] + 1e-9
     assert math.isfinite(ob.bias_neg_log_posterior(s, q))
+
+
+def test_outside_the_domain_is_reported_as_non_finite(plc):
+    m = small_mock(24, "radial_masked", sigma=1.0, nbar=1.5)
+    kb, b = mocks.bias_table(m.n, m.box, 1.4, 0.1)
+    s = m.mu + 0.3 * np.random.default_rng(24).standard_normal((m.n,) * 3)
+    assert ob.bias_neg_log_posterior(s, _bp(m, kb, b, 1.4)) == math.inf
+    c = _ctx(plc, m, "fp64", kb, b, 1.4)
+    with pytest.raises(plc.PlcError) as e:
+        c.bias_logpost_grad(dev(s, torch.float64), dev(m.N, torch.int32), dev(m.w, torch.float64),
+                            m.nbar)
+    assert e.value.status == 4
 
 
 def test_bias_map_rejects_a_start_outside_the_domain(plc):
