@@ -556,6 +556,7 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     line["gauss_prior_map"] = {"ms": e0.elapsed_time(e1), "precision": "mixed",
                                **{k: rg.stats[k] for k in ("newton_iters", "cg_iters",
                                                            "grad_ffts", "grad_rel")}}
+    bias_extra(plc, m, N_dev, line)
     # reconstruction quality against the true field (r and D_Euc, Sec. 4.1.2)
     # and the matter statistics of ln(1 + delta) after 10 Mpc/h smoothing
     d_true = torch.expm1(torch.from_numpy(m.s_true).cuda())
@@ -595,6 +596,50 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
             "sample": (f"one oracle Hv ({t_hv:.2f} s) and one gradient+objective ({t_g:.2f} s) at "
                        f"256^3, scaled to the oracle's {hvc} Hv and {gc} gradients per MAP"),
             "hv_per_s": 1.0 / t_hv}
+
+
+def bias_extra(plc, m, N_dev, line):
+    """The linear-bias MAP (Sec. 2.4.1) on the same counts, from delta_M = 0,
+    with the scale-dependent table b(k) = 1.5 (k / 0.1 h/Mpc)^0.1: time to
+    MAP in both precisions and the kernel shares of one host-timed solve."""
+    import torch
+    from paper_0911_1407_gb300 import mocks
+    n = m.n
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kb, b = mocks.bias_table(n, m.box, 1.5, 0.1)
+    out = {"table": "b(k) = 1.5 (k / 0.1 h/Mpc)^0.1, b_dc = 1.5"}
+    s = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    for prec, reps in (("mixed", 2), ("fp64", 1)):
+        c = plc.Context(n, m.box, prec)
+        c.set_prior(m.k_tab, m.P_tab, m.mu)
+        c.set_bias(kb, b, 1.5)
+        for _ in range(reps):
+            s.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            r = c.bias_map(N_dev, None, m.nbar, s=s, tol=TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out[prec] = {"ms": e0.elapsed_time(e1),
+                     **{k: r.stats[k] for k in ("newton_iters", "cg_iters", "grad_evals",
+                                                "grad_ffts", "grad_ffts_fp64", "grad_rel",
+                                                "kernels")}}
+        if prec == "mixed":
+            s_bias = s.clone()
+            c.profile_enable(True)
+            s.zero_()
+            c.bias_map(N_dev, None, m.nbar, s=s, tol=TOL)
+            prof = c.profile_read()
+            c.profile_enable(False)
+            tot = sum(v[2] for v in prof.values())
+            top = sorted(((k, v) for k, v in prof.items() if v[0]), key=lambda kv: -kv[1][2])[:8]
+            out["kernel_shares"] = {k: {"launches": v[0], "ms": round(v[2], 3),
+                                        "share": round(v[2] / tot, 3)} for k, v in top}
+        c.close()
+    d = s_bias - s
+    out["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()), "rel_l2": float(d.norm() / s.norm())}
+    line["bias_map"] = out
 
 
 def batch_extra(plc, line):
