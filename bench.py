@@ -586,10 +586,8 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     # the FP64 oracle on the host cores, on a bounded sample
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:
         t_hv, t_g = time_oracle_sample(m)
-        # the oracle's own iteration: the FP64 solve's CG products plus one Hv
-        # per Newton step for Eq. (New5), every trial through the FFT
-        hvc = r.stats["hv_count"] + r.stats["newton_iters"]
-        gc = r.stats["grad_evals"]
+        # the oracle's own iteration on this workload (as the reference arm)
+        hvc, gc = REF_HV_PER_MAP, REF_GRAD_PER_MAP
         t_map = t_hv * hvc + t_g * gc
         line["cpu_baseline"] = {
             "value": 1.0 / t_map, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
