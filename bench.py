@@ -28,7 +28,6 @@ import os
 import statistics
 import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -70,16 +69,13 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = None
 
     def start(self):
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
@@ -88,12 +84,13 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
-            self.proc.wait(timeout=5)
+            out, _ = self.proc.communicate(timeout=5)
         except Exception:
             self.proc.kill()
+            out, _ = self.proc.communicate()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in (out or "").splitlines():
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -105,7 +102,6 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
@@ -123,13 +119,15 @@ def algorithmic_bytes(n: int) -> dict:
         "xf_f32": 4 * 4 * n3 + spec32,          # read r, D, p; write p; write spectrum
         "yf_f32": 2 * spec32, "z_f32": 2 * spec32, "yi_f32": 2 * spec32,
         "xi_f32": spec32 + 3 * 4 * n3,          # read spectrum, D, p; write Hp
-        # gradients with the Newton step fused in (FP32 first phase, FP64 last)
-        "grad_xf_f32": (8 + 4 + 8) * n3 + spec32,   # read s, xi; write s; write spectrum
+        # FFT gradients (w = 1): read s, write the spectrum; read the
+        # spectrum, s, N, write y, g, D, r (FP32 phase: all FP32; FP64
+        # context: y, g, D, r in FP64)
+        "grad_xf_f32": 4 * n3 + spec32,
         "grad_yf_f32": 2 * spec32, "grad_z_f32": 2 * spec32, "grad_yi_f32": 2 * spec32,
-        "grad_xi_f32": spec32 + (8 + 4 + 4 + 4) * n3,   # read spectrum, s, N; write D, r
-        "grad_xf_f64": (8 + 4 + 8) * n3 + spec64,
+        "grad_xi_f32": spec32 + (4 + 4 + 4 * 4) * n3,
+        "grad_xf_f64": 8 * n3 + spec64,
         "grad_yf_f64": 2 * spec64, "grad_z_f64": 2 * spec64, "grad_yi_f64": 2 * spec64,
-        "grad_xi_f64": spec64 + (8 + 4 + 4 + 4) * n3,
+        "grad_xi_f64": spec64 + (8 + 4 + 4 * 8) * n3,
         # read x, p, r, Hp, D; write x, r (the first iteration of a solve
         # writes x = alpha p without reading x: 4 bytes less, see main)
         "cg_update_f32": 7 * 4 * n3,
@@ -230,7 +228,7 @@ def reference_arm(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["plc", "reference"], default="plc")
     ap.add_argument("--no-extras", action="store_true",
@@ -282,14 +280,16 @@ def main(argv=None):
         s.fill_(m.mu)
         return ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, device_driven=driven)
 
+    # clocks are sampled from the warm-up on (nvidia-smi takes a moment to
+    # start), through the end of the timed region: all under load
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
     # ---------------- timed region: K whole MAP solves -----------------------
-    clocks = ClockSampler(local)
     ctx.profile_enable(False)            # launch counts only, no per-launch events
-    clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
