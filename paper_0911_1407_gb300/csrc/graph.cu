@@ -328,14 +328,24 @@ void capture_step(plc_ctx* c, const std::vector<cudaStream_t>& st, int lv, DevCt
 
 }  // namespace
 
-// Device state of the device-driven solve of one context.
-struct GraphSolve {
-  DevCtl* ctl = nullptr;          // device
-  DevCtl* ctl_host = nullptr;     // pinned copy
-  cudaGraphExec_t exec = nullptr; // single-solve graph and its key
+// One instantiated single-solve graph and the key it was captured for.
+struct SolveExec {
+  cudaGraphExec_t exec = nullptr;
   const void* key_ptr[3] = {};
   double key_val[9] = {};
   int key_int[4] = {};
+  unsigned long long used = 0;    // last use, for eviction
+};
+
+// Device state of the device-driven solve of one context: the control block
+// and a few cached graphs (a caller that alternates between buffer sets,
+// e.g. to overlap copies with solves, relaunches each set's graph).
+struct GraphSolve {
+  static constexpr int kCache = 4;
+  DevCtl* ctl = nullptr;          // device
+  DevCtl* ctl_host = nullptr;     // pinned copy
+  SolveExec cache[kCache];
+  unsigned long long clock = 0;
 };
 
 static GraphSolve* graph_state(plc_ctx* c) {
@@ -352,7 +362,8 @@ static GraphSolve* graph_state(plc_ctx* c) {
 void graph_release(plc_ctx* c) {
   GraphSolve* g = static_cast<GraphSolve*>(c->graph);
   if (!g) return;
-  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (SolveExec& e : g->cache)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
   if (g->ctl) cudaFree(g->ctl);
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   delete g;
@@ -504,9 +515,9 @@ void fill_stats(const DevCtl& h, plc_stats* st, double ms) {
   st->ms = ms;
 }
 
-bool same_key(const GraphSolve* g, const void* const* p, const double* v, const int* k) {
-  return g->exec && std::equal(p, p + 3, g->key_ptr) && std::equal(v, v + 9, g->key_val) &&
-         std::equal(k, k + 4, g->key_int);
+bool same_key(const SolveExec& g, const void* const* p, const double* v, const int* k) {
+  return g.exec && std::equal(p, p + 3, g.key_ptr) && std::equal(v, v + 9, g.key_val) &&
+         std::equal(k, k + 4, g.key_int);
 }
 
 }  // namespace
@@ -521,27 +532,35 @@ plc_status newton_map_graph(plc_ctx* c, const int32_t* N, const double* w, doubl
                         c->jac_c, c->prior_var};
   const int ki[4] = {o.max_newton, o.max_cg, o.precond * 2 + o.start,
                      c->plan.f1 * 64 + c->plan.f2};
-  if (!same_key(gs, kp, kv, ki)) {
-    if (gs->exec) {
-      cudaGraphExecDestroy(gs->exec);
-      gs->exec = nullptr;
+  SolveExec* e = nullptr;
+  for (SolveExec& x : gs->cache)
+    if (same_key(x, kp, kv, ki)) e = &x;
+  if (!e) {
+    // capture into the least recently used slot
+    e = &gs->cache[0];
+    for (SolveExec& x : gs->cache)
+      if (x.used < e->used) e = &x;
+    if (e->exec) {
+      cudaGraphExecDestroy(e->exec);
+      e->exec = nullptr;
     }
     Streams ss;
     cudaGraph_t top;
     check(cudaGraphCreate(&top, 0), "graph create");
     try {
       capture_solve<TC>(c, top, ss.s, N, w, nbar, s_out, o);
-      check(cudaGraphInstantiate(&gs->exec, top, 0), "graph instantiate");
+      check(cudaGraphInstantiate(&e->exec, top, 0), "graph instantiate");
     } catch (...) {
       cudaGraphDestroy(top);
       throw;
     }
     cudaGraphDestroy(top);
-    std::copy(kp, kp + 3, gs->key_ptr);
-    std::copy(kv, kv + 9, gs->key_val);
-    std::copy(ki, ki + 4, gs->key_int);
+    std::copy(kp, kp + 3, e->key_ptr);
+    std::copy(kv, kv + 9, e->key_val);
+    std::copy(ki, ki + 4, e->key_int);
   }
-  check(cudaGraphLaunch(gs->exec, c->stream), "graph launch");
+  e->used = ++gs->clock;
+  check(cudaGraphLaunch(e->exec, c->stream), "graph launch");
   check(cudaMemcpyAsync(gs->ctl_host, gs->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream),
         "control block");
   check(cudaStreamSynchronize(c->stream), "stream synchronize");

@@ -37,6 +37,23 @@ def _solve(c, m, driven, **kw):
     return r
 
 
+def test_cached_graphs_for_alternating_buffers(plc):
+    """Solves that alternate between buffer sets (and more sets than the
+    cache holds) relaunch or recapture the right graph: every result equals
+    the host-driven one bit for bit."""
+    m = small_mock(32, "radial_masked", sigma=1.2, nbar=1.0)
+    c = _ctx(plc, m, "mixed")
+    ref = _solve(c, m, 0, tol=1e-6)
+    sets = [(dev(m.N, torch.int32), dev(m.w, torch.float64),
+             torch.empty((m.n,) * 3, dtype=torch.float64, device="cuda")) for _ in range(6)]
+    for k in [0, 1, 0, 1, 2, 3, 4, 5, 0, 1, 5]:
+        N, w, s = sets[k]
+        s.fill_(m.mu)
+        r = c.newton_krylov_map(N, w, m.nbar, s=s, tol=1e-6, device_driven=1)
+        assert torch.equal(s, ref.s), k
+        assert r.stats["cg_iters"] == ref.stats["cg_iters"]
+
+
 @pytest.mark.parametrize("key,precision,tol", [("plain32", "fp64", 1e-12), ("plain32", "mixed", 1e-6),
                                                ("sel48", "mixed", 1e-6), ("sel48", "fp64", 1e-10),
                                                ("production256", "mixed", 1e-6)])
