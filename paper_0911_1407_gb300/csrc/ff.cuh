@@ -63,17 +63,56 @@ __device__ __forceinline__ ff halve(ff a) { return ff(0.5f * a.hi, 0.5f * a.lo);
 
 __device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double to_double(float a) { return (double)a; }
+
+// Format conversions between double and float-float by integer operations on
+// the IEEE-754 bit fields, so that the FP64 pipe (1/64 of the FP32 rate on
+// GB300) is not used for them.
+//
+// ff_split(d): hi = d with its significand cut to 24 bits, lo = the remaining
+// 29 bits rounded to a float (exact scaling by a power of two), then one
+// Fast2Sum so that |lo| <= ulp(hi) / 2.  hi + lo equals d to 2^-48 relative.
+// |d| < 2^-149 gives 0; the narrow bands where hi or lo would leave the normal
+// float range (2^-149 <= |d| < 2^-70, |d| >= 2^128, inf, NaN) take the
+// FP64 conversion.
+__device__ __forceinline__ ff ff_split(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned top = (unsigned)(b >> 32);
+  const int e = (int)((top >> 20) & 0x7ffu) - 1023;
+  if (e < -149) return ff(0.f, 0.f);
+  if (e < -70 || e > 127) return ff(d);
+  const unsigned sign = top & 0x80000000u;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;             // 52 bits
+  const float h = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);  // 2^(e - 52), normal
+  float l = __uint2float_rn((unsigned)(mant & 0x1FFFFFFFull)) * scale;
+  if (sign) l = -l;
+  const float s = h + l;                                                // Fast2Sum, |h| >= |l|
+  return ff(s, l - (s - h));
+}
+
+// A normal float widened to double exactly (subnormals flush to 0; inf and
+// NaN take the FP64 conversion).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  if (ex == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// hi + lo rounded to double: one FP64 addition of the exact widenings.
+__device__ __forceinline__ double ff_to_double(ff a) { return widen(a.hi) + widen(a.lo); }
 __device__ __forceinline__ ff ff_abs(ff a) { return a.hi < 0.f ? -a : a; }
 
-// exp(x) of an FP64 argument in float-float, by the table-driven method of
+// exp(x) of a float-float argument, by the table-driven method of
 // Tang (ACM TOMS 15, 1989) with 64 table points: x = (64 m + j) ln2/64 + r,
 // |r| <= ln2/128, exp(x) = 2^m 2^(j/64) (1 + p(r)), p the Taylor polynomial
 // of exp(r) - 1 to degree 5 (remainder below 4e-17).  The reduction is done
 // in float-float, so the relative error is a few 2^-48 of max(|x|, 1).
 // tab[j] = 2^(j/64) in float-float (device memory, read through L1).
 // For |x| < 80.
-__device__ __forceinline__ ff exp_ff(double x, const ff* __restrict__ tab) {
-  const ff xf(x);
+__device__ __forceinline__ ff exp_ff(ff xf, const ff* __restrict__ tab) {
   const float nf = rintf(xf.hi * 92.332482616893657f);     // 64 / ln 2
   const int nn = (int)nf;
   const int j = nn & 63, m = (nn - j) / 64;

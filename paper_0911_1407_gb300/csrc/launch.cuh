@@ -175,9 +175,9 @@ void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, dou
   if constexpr (std::is_same<T, double>::value && std::is_same<TC, float>::value) {
     // the FP64 gradient of the mixed solve: float-float transforms and
     // epilogue where the length has a four-step schedule
-    const EpiGradFF epi{s, w, N, nbar, c->mu, y, g, D, r, (float)c->jac_c, jac ? 1 : 0,
+    const EpiGradFF epi{s, w, N, ff(nbar), ff(c->mu), y, g, D, r, (float)c->jac_c, jac ? 1 : 0,
                         static_cast<const ff*>(c->expff)};
-    if (run_four_step<ff>(c, ProShiftFF{s, c->mu}, epi, FinGrad{}, 0, nullptr, S_GXFF)) return;
+    if (run_four_step<ff>(c, ProShiftFF{s, ff(c->mu)}, epi, FinGrad{}, 0, nullptr, S_GXFF)) return;
   }
   run_pipeline<T>(c, ProShift<T, TS>{s, c->mu},
                   EpiGrad<T, TS, double, TC>{s, w, N, nbar, c->mu, y, g, D, r, c->jac_c,

@@ -109,25 +109,27 @@ template <typename T, bool JAC> struct ProCgDir {
   }
 };
 
-// s - mu formed in FP64 from an FP64 s and handed to float-float transforms
-// (the nearest float-float to the FP64 difference).
+// s - mu from an FP64 s, in float-float for float-float transforms: s split
+// into float-float by its bit fields, mu given as a float-float (error a few
+// 2^-48 of max(|s|, |mu|)).
 struct ProShiftFF {
   const double* s;
-  double mu;
+  ff mu;
   __device__ void prepare() {}
   __device__ void prefetch(size_t i, unsigned cnt) const { prefetch_l2(s + i, cnt * sizeof(double)); }
   __device__ V4<ff> vec4(size_t i) const {
     const V4<double> a = ld4(s + i);
-    return V4<ff>{{ff(a.v[0] - mu), ff(a.v[1] - mu), ff(a.v[2] - mu), ff(a.v[3] - mu)}};
+    return V4<ff>{{ff_split(a.v[0]) - mu, ff_split(a.v[1]) - mu, ff_split(a.v[2]) - mu,
+                   ff_split(a.v[3]) - mu}};
   }
 };
 
 // ------------------------------- epilogues --------------------------------
 // The gradient epilogue of EpiGrad for float-float transforms (the FP64
-// gradient of the mixed solve), kept in float-float so that it needs no FP64
-// arithmetic beyond format conversions: y (from the transform), s (FP64 in
-// memory), D = nbar w e^s (exp_ff), g = y + D - N and the six sums of
-// EpiGrad are float-float; y and g are stored in FP64, D and r = -g in FP32.
+// gradient of the mixed solve), kept in float-float: y (from the transform),
+// s (FP64 in memory, split by its bit fields), D = nbar w e^s (exp_ff),
+// g = y + D - N and the six sums of EpiGrad are float-float; y and g are
+// stored in FP64 (one FP64 addition each), D and r = -g in FP32.
 struct EpiGradFF {
   static constexpr int NV = 6;
   static constexpr unsigned MAXMASK = 0;
@@ -135,7 +137,7 @@ struct EpiGradFF {
   const double* s;
   const double* w;      // may be null
   const int32_t* N;
-  double nbar, mu;
+  ff nbar, mu;
   double* yout;
   double* g;
   float* D;
@@ -153,14 +155,14 @@ struct EpiGradFF {
     const V4<int32_t> nv = ld4(N + i);
     V4<double> wv{{1.0, 1.0, 1.0, 1.0}};
     if (w) wv = ld4(w + i);
-    const ff nb(nbar), m(mu);
+    const ff nb = nbar, m = mu;
     V4<double> yo, go;
     V4<float> dv, rv;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const ff st(sv.v[j]);
-      ff d = nb * exp_ff(sv.v[j], exptab);
-      if (w) d = d * ff(wv.v[j]);
+      const ff st = ff_split(sv.v[j]);
+      ff d = nb * exp_ff(st, exptab);
+      if (w) d = d * ff_split(wv.v[j]);
       const ff ni((float)nv.v[j], 0.f);    // counts below 2^24 are exact
       const ff gi = (y.v[j] + d) - ni;
       const ff ns = ni * st;
@@ -171,8 +173,8 @@ struct EpiGradFF {
       acc[4].add(ni * ff_abs(st));
       const float gc = gi.hi + gi.lo, dc = d.hi + d.lo;
       acc[5].add(ff(jac ? gc * jacobi(gc, dc, c) : gc * gc, 0.f));
-      yo.v[j] = to_double(y.v[j]);
-      go.v[j] = to_double(gi);
+      yo.v[j] = ff_to_double(y.v[j]);
+      go.v[j] = ff_to_double(gi);
       dv.v[j] = dc;
       rv.v[j] = -gc;
     }
@@ -191,8 +193,8 @@ template <typename Epi> struct EpiFF {
   Epi epi;
   __device__ void prefetch(size_t i, unsigned cnt) const { epi.prefetch(i, cnt); }
   __device__ void vec4(size_t i, const V4<ff>& y, Acc* acc) const {
-    const V4<double> yd{{to_double(y.v[0]), to_double(y.v[1]), to_double(y.v[2]),
-                         to_double(y.v[3])}};
+    const V4<double> yd{{ff_to_double(y.v[0]), ff_to_double(y.v[1]), ff_to_double(y.v[2]),
+                         ff_to_double(y.v[3])}};
     epi.vec4(i, yd, acc);
   }
 };

@@ -140,6 +140,11 @@ k4_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, const cpx<T>* __rest
   }
 }
 
+// A multiplier of the z pass in the transform arithmetic (float, or
+// float-float split from the FP64 table without the FP64 pipe).
+__device__ __forceinline__ float as_mult(float m, float) { return m; }
+__device__ __forceinline__ ff as_mult(double m, ff) { return ff_split(m); }
+
 // ---------------------------------------------------------------------------
 // Z: forward c2c along z, times M[|m|^2] = 1/(lambda_k n^3), inverse c2c,
 // in place.  grid = (n / 16, n/2+1); block (kyb, kx) owns B[kx][ky0 + c][:].
@@ -171,7 +176,8 @@ k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
     const int c = i / HM, mz = i - c * HM;
     const int ky = ky0 + c, my = min(ky, N - ky);
     const int m2 = kx * kx + my * my + mz * mz;
-    mv[j] = (i >= Gm::L * HM || (zero_dc && m2 == 0)) ? T(0.0) : T(__ldg(M + m2));
+    mv[j] = (i >= Gm::L * HM || (zero_dc && m2 == 0)) ? as_mult(TM(0), T())
+                                                       : as_mult(__ldg(M + m2), T());
   }
 #pragma unroll
   for (int j = 0; j < MI; ++j) {

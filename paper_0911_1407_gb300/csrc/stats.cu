@@ -98,8 +98,8 @@ struct EpiStoreFF {
   double* out;
   __device__ void prefetch(size_t, unsigned) const {}
   __device__ void vec4(size_t i, const V4<ff>& y, Acc*) const {
-    st4(out + i, V4<double>{{to_double(y.v[0]), to_double(y.v[1]), to_double(y.v[2]),
-                            to_double(y.v[3])}});
+    st4(out + i, V4<double>{{ff_to_double(y.v[0]), ff_to_double(y.v[1]), ff_to_double(y.v[2]),
+                            ff_to_double(y.v[3])}});
   }
 };
 
@@ -158,7 +158,7 @@ void gaussian_smooth(plc_ctx* c, const double* x, double* y, double radius, doub
   }
   // float-float transforms where the length has a four-step schedule (FP64
   // accuracy on the FP32 pipes), FP64 Stockham otherwise
-  if (!run_four_step<ff>(c, ProShiftFF{x, 0.0}, EpiStoreFF{y}, FinNone{}, 0, nullptr, S_GXFF,
+  if (!run_four_step<ff>(c, ProShiftFF{x, ff(0.f, 0.f)}, EpiStoreFF{y}, FinNone{}, 0, nullptr, S_GXFF,
                          table))
     run_pipeline<double>(c, ProLoad<double>{x}, EpiStore<double>{y}, FinNone{}, 0, nullptr, false,
                          table);
