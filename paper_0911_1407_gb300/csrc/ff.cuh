@@ -64,9 +64,10 @@ __device__ __forceinline__ ff halve(ff a) { return ff(0.5f * a.hi, 0.5f * a.lo);
 __device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double to_double(float a) { return (double)a; }
 
-// Format conversions between double and float-float by integer operations on
-// the IEEE-754 bit fields, so that the FP64 pipe (1/64 of the FP32 rate on
-// GB300) is not used for them.
+// double -> float-float by integer operations on the IEEE-754 bit fields, so
+// that the FP64 pipe (1/64 of the FP32 rate on GB300) is not used for it.
+// (The other direction, hi + lo in FP64, measured faster with the FP64
+// conversions than with integer widening.)
 //
 // ff_split(d): hi = d with its significand cut to 24 bits, lo = the remaining
 // 29 bits rounded to a float (exact scaling by a power of two), then one
@@ -90,19 +91,6 @@ __device__ __forceinline__ ff ff_split(double d) {
   return ff(s, l - (s - h));
 }
 
-// A normal float widened to double exactly (subnormals flush to 0; inf and
-// NaN take the FP64 conversion).
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  if (ex == 0) return __longlong_as_double((long long)sign);
-  if (ex == 0xffu) return (double)f;
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) |
-                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
-}
-// hi + lo rounded to double: one FP64 addition of the exact widenings.
-__device__ __forceinline__ double ff_to_double(ff a) { return widen(a.hi) + widen(a.lo); }
 __device__ __forceinline__ ff ff_abs(ff a) { return a.hi < 0.f ? -a : a; }
 
 // exp(x) of a float-float argument, by the table-driven method of

@@ -129,7 +129,7 @@ struct ProShiftFF {
 // gradient of the mixed solve), kept in float-float: y (from the transform),
 // s (FP64 in memory, split by its bit fields), D = nbar w e^s (exp_ff),
 // g = y + D - N and the six sums of EpiGrad are float-float; y and g are
-// stored in FP64 (one FP64 addition each), D and r = -g in FP32.
+// stored in FP64, D and r = -g in FP32.
 struct EpiGradFF {
   static constexpr int NV = 6;
   static constexpr unsigned MAXMASK = 0;
@@ -173,8 +173,8 @@ struct EpiGradFF {
       acc[4].add(ni * ff_abs(st));
       const float gc = gi.hi + gi.lo, dc = d.hi + d.lo;
       acc[5].add(ff(jac ? gc * jacobi(gc, dc, c) : gc * gc, 0.f));
-      yo.v[j] = ff_to_double(y.v[j]);
-      go.v[j] = ff_to_double(gi);
+      yo.v[j] = to_double(y.v[j]);
+      go.v[j] = to_double(gi);
       dv.v[j] = dc;
       rv.v[j] = -gc;
     }
@@ -193,8 +193,8 @@ template <typename Epi> struct EpiFF {
   Epi epi;
   __device__ void prefetch(size_t i, unsigned cnt) const { epi.prefetch(i, cnt); }
   __device__ void vec4(size_t i, const V4<ff>& y, Acc* acc) const {
-    const V4<double> yd{{ff_to_double(y.v[0]), ff_to_double(y.v[1]), ff_to_double(y.v[2]),
-                         ff_to_double(y.v[3])}};
+    const V4<double> yd{{to_double(y.v[0]), to_double(y.v[1]), to_double(y.v[2]),
+                         to_double(y.v[3])}};
     epi.vec4(i, yd, acc);
   }
 };

@@ -98,8 +98,8 @@ struct EpiStoreFF {
   double* out;
   __device__ void prefetch(size_t, unsigned) const {}
   __device__ void vec4(size_t i, const V4<ff>& y, Acc*) const {
-    st4(out + i, V4<double>{{ff_to_double(y.v[0]), ff_to_double(y.v[1]), ff_to_double(y.v[2]),
-                            ff_to_double(y.v[3])}});
+    st4(out + i, V4<double>{{to_double(y.v[0]), to_double(y.v[1]), to_double(y.v[2]),
+                            to_double(y.v[3])}});
   }
 };
 
