@@ -226,6 +226,30 @@ def reference_arm(args):
 # ----------------------------------------------------------------------------
 # the GPU arm
 # ----------------------------------------------------------------------------
+# ----------------------------------------------------------------------------
+# replicas over ranks (one process per GPU; no data-path collective)
+# ----------------------------------------------------------------------------
+def rank_spec(mocks, rank: int):
+    """The workload of one rank: the same configuration, its own seed and mock."""
+    return mocks.replace(mocks.WORKLOADS[WORKLOAD], seed=1 + rank, mock_id=rank)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (a timing: the slowest rank sets the pace)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, seconds: float) -> float:
+    """Solves per second over all ranks: every rank ran `steps` solves."""
+    return world * steps / seconds
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,7 +290,7 @@ def main(argv=None):
     import paper_0911_1407_gb300 as plc
     from paper_0911_1407_gb300 import mocks
 
-    spec = mocks.replace(mocks.WORKLOADS[WORKLOAD], seed=1 + rank, mock_id=rank)
+    spec = rank_spec(mocks, rank)
     m = mocks.make_mock(spec)
     n = m.n
     stream = torch.cuda.current_stream()
@@ -307,11 +331,8 @@ def main(argv=None):
     # (the host driver's launches are counted by the profiling counters)
     launches = (int(sum(v[0] for v in ctx.profile_read().values())) if args.host_driven
                 else int(sum(st["kernels"] for st in stats)))
-    if world > 1:
-        t = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    value = world * args.steps / t_dev
+    t_dev = max_over_ranks(t_dev, world, "cuda")
+    value = whole_job_rate(world, args.steps, t_dev)
 
     # ---------------- second timed region with per-launch CUDA events --------
     # (the events add a little host and device time, so `value` above is
@@ -380,10 +401,7 @@ def main(argv=None):
     e1.record(stream)
     torch.cuda.synchronize()
     t_e2e = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, world, "cuda")
 
     if rank != 0:
         if world > 1:
@@ -433,7 +451,7 @@ def main(argv=None):
                    "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (>1 GB touched per solve)"},
         "clocks": clk,
-        "e2e": {"value": world * args.steps / t_e2e, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(world, args.steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(N_host.numel() * 4),
                 "d2h_bytes_per_step": int(s_host[0].numel() * 8),
                 "overlap": "copies on a second stream, two buffer sets"},

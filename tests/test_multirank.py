@@ -1,0 +1,59 @@
+"""The multi-GPU path of bench.py on CPU: replicas over ranks, no data-path
+collective.  Two gloo ranks check that each rank gets its own workload seed,
+that the timing reduction returns the slowest rank's time on every rank, and
+the whole-job rate; the reference arm runs on rank 0 only.
+"""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_0911_1407_gb300 import mocks
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        spec = bench.rank_spec(mocks, rank)
+        t = bench.max_over_ranks(1.0 + 0.5 * rank, world, "cpu")
+        out.put((rank, spec.seed, spec.mock_id, t, bench.whole_job_rate(world, 4, t)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_the_slowest_time():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [1, 2] and [r[2] for r in res] == [0, 1]
+    assert all(r[3] == 1.5 for r in res)                  # max over ranks on every rank
+    assert all(abs(r[4] - 2 * 4 / 1.5) < 1e-12 for r in res)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0 and p.stdout.strip() == ""
