@@ -120,12 +120,14 @@ typedef struct {
                           host loop reads the device scalars after each gradient,
                           CG chunk and trial.  Same iteration either way
                           (default 1). */
-  int start;           /* plc_newton_krylov_map: 1 (default) iterates from the
-                          per-cell MAP of the same posterior with the prior
-                          replaced by its diagonal (the prior variance per cell;
-                          the Lambert-W solution of Eq. MAPLNUB cell by cell),
-                          0 from s_inout itself.  ||g0|| of the stopping test is
-                          taken at s_inout either way. */
+  int start;           /* plc_newton_krylov_map and plc_gauss_map: 1 (default)
+                          iterate from the per-cell MAP of the same posterior
+                          with the prior replaced by its diagonal (the prior
+                          variance per cell; the Lambert-W solution of
+                          Eq. MAPLNUB, resp. the domain root of the quadratic of
+                          Eq. MAPG, cell by cell), 0 from the caller's start
+                          itself.  ||g0|| of the stopping test is taken at the
+                          caller's start either way.  plc_bias_map ignores it. */
 } plc_opts;
 
 typedef struct {

@@ -171,6 +171,9 @@ template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* 
 // prior replaced by its diagonal (variance prior_var per cell), cell by cell.
 template <typename TS> void diag_start(plc_ctx* c, TS* s, const int32_t* N, const double* w,
                                        double nbar);
+// The same for the Gaussian-prior model (delta, Eq. MAPG cell by cell).
+template <typename TS> void diag_start_g(plc_ctx* c, TS* delta, const int32_t* N, const double* w,
+                                         double nbar);
 
 // Counts a launch and, when timing is on, brackets it with CUDA events.
 class LaunchScope {

@@ -26,6 +26,7 @@ template void boundary_step<float, float>(plc_ctx*, const float*, const float*, 
 template void cg_hv<float>(plc_ctx*, const float*, const float*, float*, float*, bool);
 template void vjp_amplitude<float>(plc_ctx*, const double*, const float*);
 template void diag_start<float>(plc_ctx*, float*, const int32_t*, const double*, double);
+template void diag_start_g<float>(plc_ctx*, float*, const int32_t*, const double*, double);
 template void lsq_init<float>(plc_ctx*, const int32_t*, const double*, double, float*, float*,
                               bool);
 template void cg_init<float>(plc_ctx*, const double*, const float*, float*, bool);

@@ -45,6 +45,7 @@ template void boundary_step<double, float>(plc_ctx*, const double*, const float*
 template void cg_hv<double>(plc_ctx*, const double*, const double*, double*, double*, bool);
 template void vjp_amplitude<double>(plc_ctx*, const double*, const double*);
 template void diag_start<double>(plc_ctx*, double*, const int32_t*, const double*, double);
+template void diag_start_g<double>(plc_ctx*, double*, const int32_t*, const double*, double);
 template void lsq_init<double>(plc_ctx*, const int32_t*, const double*, double, double*, double*,
                               bool);
 template void cg_init<double>(plc_ctx*, const double*, const double*, double*, bool);

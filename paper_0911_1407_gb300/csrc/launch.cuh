@@ -286,6 +286,14 @@ template <typename TS> void diag_start(plc_ctx* c, TS* s, const int32_t* N, cons
   check(cudaGetLastError(), "k_diag_start");
 }
 
+template <typename TS> void diag_start_g(plc_ctx* c, TS* delta, const int32_t* N, const double* w,
+                                         double nbar) {
+  LaunchScope ls(c, S_SETUP);
+  k_diag_start_g<TS><<<pw_blocks(c), kThreads, 0, c->stream>>>(delta, N, w, (float)nbar,
+                                                              (float)c->prior_var, c->n3());
+  check(cudaGetLastError(), "k_diag_start_g");
+}
+
 template <typename TC> void diag(plc_ctx* c, const double* s, const double* w, double nbar, TC* D) {
   LaunchScope ls(c, S_DIAG);
   k_diag<TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(s, w, nbar, D, c->n3());

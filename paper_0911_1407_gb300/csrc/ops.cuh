@@ -716,6 +716,32 @@ k_diag_start(TS* __restrict__ s, const int32_t* __restrict__ N, const double* __
   }
 }
 
+// The same start for the Gaussian-prior model (Eq. MAPG cell by cell with
+// S = sigma2 I): delta / sigma2 + nbar w - N / (1 + delta) = 0, i.e. with
+// a = sigma2 nbar w, 1 + delta = (1 - a + sqrt((1 - a)^2 + 4 sigma2 N)) / 2
+// for N > 0 (the root inside the domain; the rationalised form when
+// 1 - a < 0) and delta = -a for N = 0 (no logarithm: a linear term).
+template <typename TS>
+__global__ void __launch_bounds__(kThreads)
+k_diag_start_g(TS* __restrict__ delta, const int32_t* __restrict__ N,
+               const double* __restrict__ w, float nbar, float sigma2, size_t n3) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n3;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float a = sigma2 * nbar * (w ? (float)w[i] : 1.f);
+    const int ni = N[i];
+    float d;
+    if (ni > 0) {
+      const float q = 1.f - a, sn = 4.f * sigma2 * (float)ni;
+      const float r = sqrtf(q * q + sn);
+      const float u = q >= 0.f ? 0.5f * (q + r) : 0.5f * sn / (r - q);
+      d = u - 1.f;
+    } else {
+      d = -a;
+    }
+    delta[i] = (TS)d;
+  }
+}
+
 template <typename TD, typename TS>
 __global__ void __launch_bounds__(kThreads)
 k_convert(const TS* __restrict__ src, TD* __restrict__ dst, size_t n3) {

@@ -95,7 +95,10 @@ struct State {
 // boundary, tau <= 0.99 / max(-xi / (1 + delta)).
 struct Lognormal {
   static constexpr bool kBoundary = false;
-  static constexpr bool kDiagStart = true;
+  template <typename TS>
+  static void start(plc_ctx* c, TS* s, const int32_t* N, const double* w, double nbar) {
+    diag_start<TS>(c, s, N, w, nbar);
+  }
   template <typename T, typename TS, typename TC>
   static void gradient(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar,
                        T* y, T* g, TC* D, TC* r, bool jac) {
@@ -110,7 +113,10 @@ struct Lognormal {
 };
 struct GaussPrior {
   static constexpr bool kBoundary = true;
-  static constexpr bool kDiagStart = false;
+  template <typename TS>
+  static void start(plc_ctx* c, TS* s, const int32_t* N, const double* w, double nbar) {
+    diag_start_g<TS>(c, s, N, w, nbar);
+  }
   template <typename T, typename TS, typename TC>
   static void gradient(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar,
                        T* y, T* g, TC* D, TC* r, bool jac) {
@@ -191,10 +197,10 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
   GradSums gs = fft_gradient();
   const double g0 = o.g0_norm > 0.0 ? o.g0_norm : std::sqrt(gs.gg);
   S.g0_norm = g0;
-  if (Model::kDiagStart && o.start == 1) {
+  if (o.start == 1) {
     // iterate from the per-cell diagonal-prior MAP (g0 stays at s_in)
-    if (fp64) diag_start<double>(c, as<double>(cur.s), N, w, nbar);
-    else if constexpr (kMixed) diag_start<float>(c, as<float>(cur.s), N, w, nbar);
+    if (fp64) Model::template start<double>(c, as<double>(cur.s), N, w, nbar);
+    else if constexpr (kMixed) Model::template start<float>(c, as<float>(cur.s), N, w, nbar);
     gs = fft_gradient();
   }
   plc_status status = PLC_OK;

@@ -155,3 +155,24 @@ def test_gauss_map_full_size_is_a_map_for_the_oracle(plc, key, precision):
     assert rel < 1e-6
     assert abs(rel - r.stats["grad_rel"]) <= 1e-3 * r.stats["grad_rel"]
     assert np.all(1.0 + d[m.N > 0] > 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gauss_map_start_option(plc, precision):
+    """From delta = 0 (start = 0) or from the per-cell diagonal-prior MAP
+    (start = 1): the same MAP, with ||g0|| taken at delta = 0 both times."""
+    m = _gauss_mock("g32")
+    ref = _gauss_ref("g32", m)
+    c = _ctx(plc, m, precision)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    out = {}
+    for start in (0, 1):
+        r = c.gauss_map(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=tol,
+                        start=start)
+        assert r.stats["grad_rel"] < tol
+        out[start] = (host(r.s), r.stats)
+    assert out[0][1]["g0_norm"] == out[1][1]["g0_norm"]
+    bar = 1e-10 if precision == "fp64" else 1e-4
+    for start in (0, 1):
+        d = out[start][0]
+        assert np.max(np.abs(d - ref.delta) / np.maximum(np.abs(ref.delta), 1.0)) <= bar
