@@ -73,6 +73,8 @@ struct DevScalars {
   double tau;
   // fraction-to-boundary quantity of the Gaussian-prior model (k_boundary)
   double bmax;
+  // k_g0_at_mean: 1 when the start point differs from the prior mean somewhere
+  int off_mean;
 };
 
 template <typename C> __device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {

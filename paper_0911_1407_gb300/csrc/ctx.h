@@ -171,6 +171,11 @@ template <typename TD, typename TS> void convert(plc_ctx* c, const TS* src, TD* 
 // prior replaced by its diagonal (variance prior_var per cell), cell by cell.
 template <typename TS> void diag_start(plc_ctx* c, TS* s, const int32_t* N, const double* w,
                                        double nbar);
+// ||g||^2 at the prior mean (s equal to `mean` bit for bit), where the prior
+// term vanishes and g = factor w - N: into red[2], and off_mean = 1 when s
+// differs from the mean anywhere.
+void g0_at_mean(plc_ctx* c, const double* s, const int32_t* N, const double* w, double mean,
+                double factor);
 // The same for the Gaussian-prior model (delta, Eq. MAPG cell by cell).
 template <typename TS> void diag_start_g(plc_ctx* c, TS* delta, const int32_t* N, const double* w,
                                          double nbar);

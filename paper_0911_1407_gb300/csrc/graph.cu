@@ -71,7 +71,13 @@ __device__ __forceinline__ double scale_of(const DevScalars* sc) {
   return (sc->red[1] + sc->red[3]) + sc->red[4] + fabs(f_of(sc));
 }
 
-__global__ void k_ctl_init(DevCtl* t, const DevScalars* sc, CtlOpts o, Handle h_newton, int nk) {
+// first: 0 the gradient at the caller's start ran, 1 it ran when the start
+// was off the prior mean (off_mean), 2 it did not run; nk_first: its kernels
+// when it ran conditionally.  g0 comes from red[2]: that gradient's, or the
+// transform-free one at the prior mean.
+__global__ void k_ctl_init(DevCtl* t, const DevScalars* sc, CtlOpts o, Handle h_newton, int nk,
+                           int first, int nk_first) {
+  const int ran = first == 0 ? 1 : (first == 1 ? sc->off_mean : 0);
   t->tol = o.tol;
   t->mixed_switch = o.mixed_switch;
   t->eta_max = o.eta_max;
@@ -87,13 +93,18 @@ __global__ void k_ctl_init(DevCtl* t, const DevScalars* sc, CtlOpts o, Handle h_
   t->it = t->q = t->par = t->stop = t->loops = t->cg_count = 0;
   t->status = PLC_OK;
   t->cg_iters = 0;
-  t->grad_evals = 1;
-  t->grad_ffts = 1;
-  t->grad_ffts_fp64 = o.fp64 ? 1 : 0;
-  t->kernels = nk;
+  t->grad_evals = ran;
+  t->grad_ffts = ran;
+  t->grad_ffts_fp64 = ran && o.fp64 ? 1 : 0;
+  t->kernels = nk + (first == 1 && ran ? nk_first : 0);
   t->grad_rel = 0.0;
   t->neg_logpost = 0.0;
   cudaGraphSetConditional(h_newton, 1);
+}
+
+// The first gradient runs only when the start is off the prior mean.
+__global__ void k_ctl_first(const DevScalars* sc, Handle h_first) {
+  cudaGraphSetConditional(h_first, sc->off_mean ? 1u : 0u);
 }
 
 // A second FFT gradient at the start point (the first one gave g0).
@@ -385,7 +396,7 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   const Fields f32a{F[0], F[2], F[4], F[6], F[8]}, f32b{F[1], F[3], F[5], F[7], F[9]};
   const Fields f64a{s_out, F[2], F[4], F[6], F[8]}, f64b{F[1], F[3], F[5], F[7], F[9]};
 
-  Handle h_newton, h_switch, h_step;
+  Handle h_newton, h_switch, h_step, h_first;
   StepHandles hs;
   auto mk = [&](Handle* h) {
     check(cudaGraphConditionalHandleCreate(h, top, 0, cudaGraphCondAssignDefault), "handle");
@@ -393,6 +404,10 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   mk(&h_newton);
   mk(&h_switch);
   mk(&h_step);
+  // the first gradient's IF node, when there is one (a handle must belong to
+  // a conditional node for the graph to instantiate)
+  const int first = o.start != 1 ? 0 : (o.g0_norm > 0.0 ? 2 : 1);
+  if (first == 1) mk(&h_first);
   const int nvar = kMixed ? 4 : 2;
   for (int v = 0; v < nvar; ++v) {
     mk(&hs.cg[v]);
@@ -406,17 +421,39 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   capture_into(c, top, st[0], [&]() {
     const long long k0 = total_launches(c);
     reset_ticket(c);
-    if (start64) {
-      grad_newton<double, double, TC>(c, s_out, w, N, nbar, as<double>(f64a.y), as<double>(f64a.g),
-                                      as<TC>(f64a.D), as<TC>(f64a.r), jac);
-    } else if constexpr (kMixed) {
-      convert<float, double>(c, s_out, as<float>(f32a.s));
-      grad_newton<float, float, float>(c, as<float>(f32a.s), w, N, nbar, as<float>(f32a.y),
-                                       as<float>(f32a.g), as<float>(f32a.D), as<float>(f32a.r),
-                                       jac);
+    auto first_gradient = [&]() {
+      if (start64) {
+        grad_newton<double, double, TC>(c, s_out, w, N, nbar, as<double>(f64a.y),
+                                        as<double>(f64a.g), as<TC>(f64a.D), as<TC>(f64a.r), jac);
+      } else if constexpr (kMixed) {
+        convert<float, double>(c, s_out, as<float>(f32a.s));
+        grad_newton<float, float, float>(c, as<float>(f32a.s), w, N, nbar, as<float>(f32a.y),
+                                         as<float>(f32a.g), as<float>(f32a.D),
+                                         as<float>(f32a.r), jac);
+      }
+    };
+    // ||g0|| at the caller's start; with the diagonal start the gradient
+    // there serves only this norm: none when g0_norm is given, and at the
+    // prior mean the transform-free one (the FFT gradient runs, in an IF
+    // node, only when the start is off the mean)
+    int nk_first = 0, nk_ctl = 1;
+    if (first == 1) {
+      nk_ctl = 2;
+      g0_at_mean(c, s_out, N, w, c->mu, nbar * std::exp(c->mu));
+      k_ctl_first<<<1, 1, 0, c->stream>>>(c->sc, h_first);
+      check(cudaGetLastError(), "k_ctl_first");
+      cudaGraph_t fbody;
+      add_conditional(c->stream, h_first, cudaGraphCondTypeIf, 1, &fbody);
+      capture_into(c, fbody, st[1], [&]() {
+        const long long k1 = total_launches(c);
+        first_gradient();
+        nk_first = (int)(total_launches(c) - k1);
+      });
+    } else if (first == 0) {
+      first_gradient();
     }
-    const int nk = (int)(total_launches(c) - k0) + 1;
-    k_ctl_init<<<1, 1, 0, c->stream>>>(t, c->sc, co, h_newton, nk);
+    const int nk = (int)(total_launches(c) - k0) - nk_first + nk_ctl;
+    k_ctl_init<<<1, 1, 0, c->stream>>>(t, c->sc, co, h_newton, nk, first, nk_first);
     check(cudaGetLastError(), "k_ctl_init");
     if (o.start == 1) {
       // iterate from the per-cell diagonal-prior MAP (g0 stays at s_in)

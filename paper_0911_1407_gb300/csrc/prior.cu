@@ -1,6 +1,8 @@
 // prior.cu -- device set-up of the prior operator (Sec. 2.2): the inverse
 // eigenvalue 1/(lambda n^3) for every |m|^2 of the grid and the Jacobi
 // constant (S^-1)_ii; plus the small host helpers shared by the solver.
+#include <cstring>
+
 #include "launch.cuh"
 
 namespace plc {
@@ -162,6 +164,60 @@ void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int n
   read_scalars(c);
   c->jac_c = c->sc_host->red[0];
   c->prior_var = c->sc_host->red[1];
+}
+
+// ||g||^2 at the prior mean without a transform: at s = mean the prior term
+// S^-1 (s - mean) vanishes and g = factor w - N (lognormal model: mean mu,
+// factor nbar e^mu; Gaussian-prior model: mean 0, factor nbar).  Also sets
+// off_mean when s differs from the mean anywhere (compared bit for bit, so
+// -0.0 against +0.0 counts as different: the caller then takes the
+// transform).  ||g0|| only normalises the stop test: the Kahan FP32 sum
+// (relative error ~1e-7) is ample.
+__global__ void __launch_bounds__(kThreads)
+k_g0_at_mean(const double* __restrict__ s, const int32_t* __restrict__ N,
+             const double* __restrict__ w, long long mean_bits, float factor, size_t n3,
+             RedArgs ra) {
+  AccK acc[2];
+  acc[0].init(false);
+  acc[1].init(true);
+  const size_t step = (size_t)gridDim.x * blockDim.x * 4;
+  for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < n3; i += step) {
+    const V4<int32_t> nv = ld4(N + i);
+    V4<float> wv{{1.f, 1.f, 1.f, 1.f}};
+    if (w) {
+      const V4<double> wd = ld4(w + i);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) wv.v[j] = (float)wd.v[j];
+    }
+    const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(s + i));
+    const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(s + i) + 1);
+    const bool off = a.x != mean_bits || a.y != mean_bits || b.x != mean_bits || b.y != mean_bits;
+    acc[1].max(off ? 1.f : 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float d = factor * wv.v[j] - (float)nv.v[j];
+      acc[0].add(d * d);
+    }
+  }
+  struct Fin {
+    __device__ void operator()(const double* t, DevScalars* sc) const {
+      sc->red[2] = t[0];
+      sc->off_mean = t[1] > 0.0 ? 1 : 0;
+    }
+  };
+  block_reduce_finish_acc<2, 2u>(acc, ra, Fin{});
+}
+
+// ||g(mean)||^2 into red[2] and the off_mean flag (see k_g0_at_mean).
+void g0_at_mean(plc_ctx* c, const double* s, const int32_t* N, const double* w,
+                       double mean, double factor) {
+  LaunchScope ls(c, S_SETUP);
+  long long bits;
+  static_assert(sizeof(bits) == sizeof(mean), "double is 64 bits");
+  memcpy(&bits, &mean, sizeof(bits));
+  k_g0_at_mean<<<pw_blocks(c), kThreads, 0, c->stream>>>(s, N, w, bits, (float)factor, c->n3(),
+                                                         red_args(c));
+  check(cudaGetLastError(), "k_g0_at_mean");
 }
 
 void build_bias(plc_ctx* c, const double* lk_host, const double* lb_host, int nb, double b_dc) {

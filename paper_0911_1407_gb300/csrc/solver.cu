@@ -95,6 +95,11 @@ struct State {
 // boundary, tau <= 0.99 / max(-xi / (1 + delta)).
 struct Lognormal {
   static constexpr bool kBoundary = false;
+  // ||g||^2 at the prior mean mu, where S^-1 (s - mu) = 0: g = nbar w e^mu - N
+  static void g0_at_mean(plc_ctx* c, const double* s, const int32_t* N, const double* w,
+                         double nbar) {
+    plc::g0_at_mean(c, s, N, w, c->mu, nbar * std::exp(c->mu));
+  }
   template <typename TS>
   static void start(plc_ctx* c, TS* s, const int32_t* N, const double* w, double nbar) {
     diag_start<TS>(c, s, N, w, nbar);
@@ -113,6 +118,11 @@ struct Lognormal {
 };
 struct GaussPrior {
   static constexpr bool kBoundary = true;
+  // ||g||^2 at delta = 0, the prior mean: g = nbar w - N
+  static void g0_at_mean(plc_ctx* c, const double* s, const int32_t* N, const double* w,
+                         double nbar) {
+    plc::g0_at_mean(c, s, N, w, 0.0, nbar);
+  }
   template <typename TS>
   static void start(plc_ctx* c, TS* s, const int32_t* N, const double* w, double nbar) {
     diag_start_g<TS>(c, s, N, w, nbar);
@@ -191,11 +201,31 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
   };
 
   reset_ticket(c);
-  if (!fp64) {
-    if constexpr (kMixed) convert<float, double>(c, s_out, as<float>(cur.s));
+  // ||g0|| at the caller's start.  With the diagonal start the gradient
+  // there serves only this norm: none is taken when g0_norm is given, and
+  // at the prior mean it needs no transform.
+  GradSums gs{};
+  double g0 = o.g0_norm;
+  bool first = true;
+  if (o.start == 1) {
+    if (g0 > 0.0) {
+      first = false;
+    } else {
+      Model::g0_at_mean(c, s_out, N, w, nbar);
+      read_scalars(c);
+      if (!c->sc_host->off_mean) {
+        g0 = std::sqrt(c->sc_host->red[2]);
+        first = false;
+      }
+    }
   }
-  GradSums gs = fft_gradient();
-  const double g0 = o.g0_norm > 0.0 ? o.g0_norm : std::sqrt(gs.gg);
+  if (first) {
+    if (!fp64) {
+      if constexpr (kMixed) convert<float, double>(c, s_out, as<float>(cur.s));
+    }
+    gs = fft_gradient();
+    if (!(g0 > 0.0)) g0 = std::sqrt(gs.gg);
+  }
   S.g0_norm = g0;
   if (o.start == 1) {
     // iterate from the per-cell diagonal-prior MAP (g0 stays at s_in)

@@ -171,7 +171,8 @@ def test_gauss_map_start_option(plc, precision):
                         start=start)
         assert r.stats["grad_rel"] < tol
         out[start] = (host(r.s), r.stats)
-    assert out[0][1]["g0_norm"] == out[1][1]["g0_norm"]
+    # start = 1 takes ||g(0)|| = ||nbar w - N|| without a transform
+    assert abs(out[0][1]["g0_norm"] - out[1][1]["g0_norm"]) <= 1e-6 * out[0][1]["g0_norm"]
     bar = 1e-10 if precision == "fp64" else 1e-4
     for start in (0, 1):
         d = out[start][0]

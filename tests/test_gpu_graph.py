@@ -37,6 +37,29 @@ def _solve(c, m, driven, **kw):
     return r
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_start_off_the_prior_mean(plc, precision):
+    """A start point off mu takes the FFT gradient there for ||g0|| (the IF
+    node of the device-driven graph); both drivers agree bit for bit, and
+    a start at mu needs no transform for ||g0||."""
+    m = small_mock(32, "radial_masked", sigma=1.2, nbar=1.0)
+    c = _ctx(plc, m, precision)
+    s0 = torch.full((m.n,) * 3, m.mu, dtype=torch.float64, device="cuda")
+    s0[5, 6, 7] += 0.25
+    out = []
+    for driven in (0, 1):
+        s = s0.clone()
+        r = c.newton_krylov_map(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, s=s,
+                                tol=1e-6, device_driven=driven)
+        out.append(r)
+    for k in ITER_KEYS:
+        assert out[0].stats[k] == out[1].stats[k], k
+    assert torch.equal(out[0].s, out[1].s)
+    at_mean = _solve(c, m, 1, tol=1e-6)
+    assert out[1].stats["grad_ffts"] == at_mean.stats["grad_ffts"] + 1
+    assert out[1].stats["g0_norm"] != at_mean.stats["g0_norm"]
+
+
 def test_cached_graphs_for_alternating_buffers(plc):
     """Solves that alternate between buffer sets (and more sets than the
     cache holds) relaunch or recapture the right graph: every result equals

@@ -165,7 +165,9 @@ def test_map_mixed_to_fp64_accuracy(plc, key):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_map_start_point_option(plc, precision):
     """The diagonal-prior start (opts.start = 1) reaches the same MAP as the
-    start at mu with fewer Newton steps; ||g0|| is taken at mu in both."""
+    start at mu with fewer Newton steps; ||g0|| is taken at mu in both (with
+    start = 1 by the transform-free form g(mu) = nbar w e^mu - N, summed in
+    compensated FP32, so equal to ~1e-7)."""
     m = mocks.make_mock(mocks.WORKLOADS["adjoint128"])
     c = plc.Context(m.n, m.box, precision)
     c.set_prior(m.k_tab, m.P_tab, m.mu)
@@ -173,8 +175,8 @@ def test_map_start_point_option(plc, precision):
     tol = 1e-10 if precision == "fp64" else 1e-6
     r0 = c.newton_krylov_map(Nd, None, m.nbar, tol=tol, start=0)
     r1 = c.newton_krylov_map(Nd, None, m.nbar, tol=tol, start=1)
-    assert r0.stats["g0_norm"] == r1.stats["g0_norm"]
+    assert abs(r0.stats["g0_norm"] - r1.stats["g0_norm"]) <= 1e-6 * r0.stats["g0_norm"]
     assert r1.stats["newton_iters"] < r0.stats["newton_iters"]
-    assert r1.stats["grad_ffts"] == r0.stats["grad_ffts"] + 1
+    assert r1.stats["grad_ffts"] == r0.stats["grad_ffts"]      # no transform for g(mu)
     bar = 1e-8 if precision == "fp64" else 1e-4
     assert np.max(np.abs(host(r0.s) - host(r1.s))) <= bar
