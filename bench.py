@@ -138,6 +138,37 @@ def algorithmic_bytes(n: int) -> dict:
     }
 
 
+def bias_bytes(n: int) -> dict:
+    """Algorithmic bytes per launch of the linear-bias model's FP32 passes,
+    averaged over the three pipelines of its CG product (B(E p) -> Q .,
+    B(.) -> E ., S^-1 p + d1 p + .): the mix of nearly all its launches."""
+    n3, h = n ** 3, n // 2 + 1
+    spec = 8 * h * n * n
+    return {"bias_xf_f32": (28 * n3 + 3 * spec) / 3, "bias_yf_f32": 2 * spec,
+            "bias_z_f32": 2 * spec, "bias_yi_f32": 2 * spec,
+            "bias_xi_f32": (32 * n3 + 3 * spec) / 3, "cg_update_f32": 7 * 4 * n3}
+
+
+def dominant_kernel(ctx, run, nbytes: dict) -> dict:
+    """Run `run()` once with per-launch CUDA events on (`run` should enqueue
+    one CG iteration per chunk, so that no launch is an early exit that would
+    pull the mean down); the kernel kind with
+    the most device time, its mean duration and, where its algorithmic bytes
+    per launch are known, the achieved bandwidth against the measured peak."""
+    ctx.profile_enable(True)
+    run()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    tot = sum(v[2] for v in prof.values())
+    k, (nl, nt, ms) = max(prof.items(), key=lambda kv: kv[1][2])
+    avg_us = 1e3 * ms / nt if nt else None
+    out = {"kernel": k, "share": ms / tot if tot else None, "avg_us": avg_us, "launches": nl}
+    if k in nbytes and avg_us:
+        gbs = nbytes[k] / (avg_us * 1e-6) / 1e9
+        out.update({"achieved_gbs": gbs, "frac": gbs / peaks()[0], "peak": "measured hbm_gbs"})
+    return out
+
+
 def fft_flops(n: int) -> float:
     """5 N log2 N per complex line transform of length n."""
     return 5.0 * n * math.log2(n)
@@ -594,6 +625,9 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
         torch.cuda.synchronize()
         lsq[prec] = {"ms": e0.elapsed_time(e1), "cg_iters": st["cg_iters"],
                      "rel_residual": st["grad_rel"]}
+    lsq["dominant_mixed"] = dominant_kernel(
+        ctx, lambda: ctx.wiener_lsq(N_dev, None, m.nbar, tol=1e-6, cg_chunk=1),
+        algorithmic_bytes(n))
     line["lsq_wiener"] = lsq
     # the Gaussian-prior Poisson MAP (Eq. MAPG) on the same data, from delta = 0
     dg = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
@@ -607,6 +641,10 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     line["gauss_prior_map"] = {"ms": e0.elapsed_time(e1), "precision": "mixed",
                                **{k: rg.stats[k] for k in ("newton_iters", "cg_iters",
                                                            "grad_ffts", "grad_rel")}}
+    dg2 = torch.zeros_like(dg)
+    line["gauss_prior_map"]["dominant"] = dominant_kernel(
+        ctx, lambda: ctx.gauss_map(N_dev, None, m.nbar, delta=dg2.zero_(), tol=TOL, cg_chunk=1),
+        algorithmic_bytes(n))
     bias_extra(plc, m, N_dev, line)
     # reconstruction quality against the true field (r and D_Euc, Sec. 4.1.2)
     # and the matter statistics of ln(1 + delta) after 10 Mpc/h smoothing
@@ -678,13 +716,21 @@ def bias_extra(plc, m, N_dev, line):
             s_bias = s.clone()
             c.profile_enable(True)
             s.zero_()
-            c.bias_map(N_dev, None, m.nbar, s=s, tol=TOL)
+            # one CG iteration per chunk: no launch is an early exit
+            c.bias_map(N_dev, None, m.nbar, s=s, tol=TOL, cg_chunk=1)
             prof = c.profile_read()
             c.profile_enable(False)
             tot = sum(v[2] for v in prof.values())
             top = sorted(((k, v) for k, v in prof.items() if v[0]), key=lambda kv: -kv[1][2])[:8]
             out["kernel_shares"] = {k: {"launches": v[0], "ms": round(v[2], 3),
                                         "share": round(v[2] / tot, 3)} for k, v in top}
+            k0, v0 = top[0]
+            nb = bias_bytes(n).get(k0)
+            if nb and v0[1]:
+                avg_us = 1e3 * v0[2] / v0[1]
+                gbs = nb / (avg_us * 1e-6) / 1e9
+                out["dominant"] = {"kernel": k0, "avg_us": avg_us, "achieved_gbs": gbs,
+                                   "frac": gbs / peaks()[0], "bytes": "CG-product mix average"}
         c.close()
     d = s_bias - s
     out["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()), "rel_l2": float(d.norm() / s.norm())}
