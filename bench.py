@@ -246,7 +246,8 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_map, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": 256, "box": 500.0, "sigma_G": 1.8, "nbar": 1.0},
+            "config": workload_config(args.gpus),
+            "precision": "FP64 throughout (the oracle)",
             "cpu_baseline": {"value": 1.0 / t_map, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": 1.0 / t_map, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -260,6 +261,16 @@ def reference_arm(args):
 # ----------------------------------------------------------------------------
 # replicas over ranks (one process per GPU; no data-path collective)
 # ----------------------------------------------------------------------------
+def workload_config(world: int) -> dict:
+    """The `config` of the JSON line, the same for both arms."""
+    from paper_0911_1407_gb300 import mocks
+    spec = mocks.WORKLOADS[WORKLOAD]
+    return {"workload": WORKLOAD, "n": spec.n, "box": spec.box, "sigma_G": spec.sigma_G,
+            "nbar": spec.nbar, "w": 1, "pk_bins": spec.nbins, "tol": TOL,
+            "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (>1 GB touched per solve)"}
+
+
 def rank_spec(mocks, rank: int):
     """The workload of one rank: the same configuration, its own seed and mock."""
     return mocks.replace(mocks.WORKLOADS[WORKLOAD], seed=1 + rank, mock_id=rank)
@@ -476,11 +487,8 @@ def main(argv=None):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "box": m.box, "sigma_G": spec.sigma_G,
-                   "nbar": m.nbar, "w": 1, "pk_bins": spec.nbins, "tol": TOL,
-                   "precision": "mixed (FP32 FFT/CG, FP64 gradient, reductions, state)",
-                   "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (>1 GB touched per solve)"},
+        "config": workload_config(world),
+        "precision": "mixed (FP32 FFT/CG, FP64-accurate gradient, FP64 reductions and state)",
         "clocks": clk,
         "e2e": {"value": whole_job_rate(world, args.steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": int(N_host.numel() * 4),
