@@ -390,8 +390,19 @@ template <typename Epi> struct EpiUnroll<Epi, decltype((void)Epi::kUnroll)> {
 // (projection onto real fields).  The epilogue sees y = (S^-1 x)_i per cell
 // and accumulates Epi::NV sums; Fin runs once on the grid totals.
 // ---------------------------------------------------------------------------
+// Resident blocks per SM the x-inverse pass asks the compiler for: 1 (no
+// register cap) except for the float-float gradient epilogue, which at 3
+// blocks (80 registers, 32 bytes of spill; shared memory allows 3) measured
+// 471 us against 598 at 2 blocks (128 registers) for 256^3.
+template <typename Epi> struct XiMinBlocks {
+  static constexpr int value = 1;
+};
+template <> struct XiMinBlocks<EpiGradFF> {
+  static constexpr int value = 3;
+};
+
 template <typename T, int N1, int N2, typename Epi, typename Fin>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, XiMinBlocks<Epi>::value)
 k4_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
       const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
   PLC_PASS4_PROLOGUE(T* R = reinterpret_cast<T*>(tw2 + N); C* X = tw2 + N);
