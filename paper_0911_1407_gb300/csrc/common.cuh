@@ -485,10 +485,11 @@ __device__ __forceinline__ void block_reduce_finish_acc(Acc* a, const RedArgs& r
 }
 
 // Grid size for element-wise kernels: a fixed multiple of the SM count so
-// that reductions are reproducible for a given problem size.
-inline int pointwise_blocks(long long nelem, int sms) {
+// that reductions are reproducible for a given problem size.  per_sm = 4 is
+// one wave of a kernel that fits 4 blocks per SM.
+inline int pointwise_blocks(long long nelem, int sms, int per_sm = 8) {
   long long want = (nelem + kThreads * 4 - 1) / (kThreads * 4);
-  long long cap = (long long)sms * 8;
+  long long cap = (long long)sms * per_sm;
   if (want > cap) want = cap;
   if (want < 1) want = 1;
   return (int)want;
