@@ -683,18 +683,19 @@ k_diag(const double* __restrict__ s, const double* __restrict__ w, double nbar,
 // Lambert W of x = e^L from L = ln x (x up to e^300 and beyond), in FP32:
 // Newton's method on w + ln w = L, the defining equation w e^w = x in log
 // form, from w = x / (1 + x) (L < 1) or w = L - ln L (L >= 1); four steps
-// reach FP32 accuracy.  L = -inf gives 0.
+// reach FP32 accuracy (fast division: the iteration corrects its rounding).
+// L = -inf gives 0.
 __device__ __forceinline__ float lambert_w_log(float L) {
   if (L == -INFINITY) return 0.f;
   float w;
   if (L < 1.f) {
     const float x = __expf(L);
-    w = x / (1.f + x);
+    w = __fdividef(x, 1.f + x);
   } else {
     w = L - __logf(L);
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) w = w * (1.f + L - __logf(w)) / (1.f + w);
+  for (int k = 0; k < 4; ++k) w = __fdividef(w * (1.f + L - __logf(w)), 1.f + w);
   return w;
 }
 

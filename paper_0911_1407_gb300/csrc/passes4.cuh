@@ -294,8 +294,19 @@ __device__ __forceinline__ void st_pair(ffc* p, ffc a, ffc b) {
 // Z = FFT(row_2c + i row_2c+1): X_a[k] = (Z[k] + conj Z[N-k]) / 2 and
 // X_b[k] = (Z[k] - conj Z[N-k]) / 2i, stored as a pair at A[z][k][y0+2c].
 // ---------------------------------------------------------------------------
+// Resident blocks per SM the x-forward pass asks the compiler for: 1 (no
+// register cap) except for the float-float prologue of the refresh gradient,
+// which at 3 blocks (80 registers, shared memory allows 3) measured 152 us
+// against 164 at 2 (89 registers) for 256^3.
+template <typename Pro> struct XfMinBlocks {
+  static constexpr int value = 1;
+};
+template <> struct XfMinBlocks<ProShiftFF> {
+  static constexpr int value = 3;
+};
+
 template <typename T, int N1, int N2, typename Pro>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, XfMinBlocks<Pro>::value)
 k4_xf(Pro pro, cpx<T>* __restrict__ A, const cpx<T>* __restrict__ twg,
       const int* __restrict__ done) {
   PLC_PASS4_PROLOGUE(T* R = reinterpret_cast<T*>(tw2 + N); C* X = tw2 + N);
