@@ -593,6 +593,33 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
     line["time_to_map_s"] = {"mixed": line["ms_per_step"] / 1e3, "fp64": t64}
     line["fp64_solve"] = {k: r.stats[k] for k in ("newton_iters", "cg_iters", "grad_evals",
                                                   "grad_ffts", "grad_rel")}
+    # the FP64 form is bound by the FP64 pipe: its dominant kernel against
+    # the FP64 rate measured here with cuBLAS DGEMM (4096^3 through
+    # torch.matmul; MEASURED_PEAKS.json has no FP64 figure) and the nominal one
+    a = torch.randn((4096, 4096), dtype=torch.float64, device="cuda")
+    b = torch.randn((4096, 4096), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        torch.matmul(a, b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dgemm = 5 * 2 * 4096 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    del a, b
+    s64b = torch.empty_like(s64)
+    dom = dominant_kernel(ctx64, lambda: ctx64.newton_krylov_map(
+        N_dev, None, m.nbar, s=s64b.fill_(m.mu), tol=TOL, device_driven=0, cg_chunk=1),
+        {"cg_update_f64": 7 * 8 * n ** 3})
+    fl = algorithmic_flops_f64(n).get(dom["kernel"])
+    if fl and dom.get("avg_us"):
+        ach = fl / (dom["avg_us"] * 1e-6) / 1e12
+        dom.update({"achieved_tflops": ach, "frac_of_dgemm": ach / dgemm,
+                    "frac_of_nominal": ach / FP64_PEAK_TFLOPS})
+    line["fp64_solve"]["dominant"] = dom
+    line["fp64_peak_measured"] = {"tflops": dgemm, "how": "cuBLAS DGEMM 4096^3 (torch.matmul)",
+                                  "nominal_tflops": FP64_PEAK_TFLOPS}
     line["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()),
                              "rel_l2": float(d.norm() / s64.norm())}
     # the FP32 -> FP64 switch point of the mixed solve
