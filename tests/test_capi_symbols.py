@@ -90,3 +90,27 @@ def test_bias_validation_without_gpu(lib):
     assert lib.plc_bias_logpost_grad(None, None, None, None, 1.0, None, None) == 1
     lib.plc_bias_hessvec.argtypes = [P] * 4 + [D, P, P]
     assert lib.plc_bias_hessvec(None, None, None, None, 1.0, None, None) == 1
+
+
+def test_header_is_plain_c_and_links(lib):
+    """include/plc.h compiles as C99 with -pedantic, and a C program links
+    against libplc.so and calls a host-only entry point.  Built in the
+    package's (ignored) build directory."""
+    import pathlib
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    work = pathlib.Path(ROOT) / "paper_0911_1407_gb300" / "_build" / "ctest"
+    work.mkdir(parents=True, exist_ok=True)
+    src = work / "t.c"
+    src.write_text('#include "plc.h"\n'
+                   'int main(void) { plc_opts o; if (plc_default_opts(&o) != PLC_OK) return 2;\n'
+                   '  return (o.max_newton > 0 && o.tol > 0.0 && o.device_driven == 1) ? 0 : 1; }\n')
+    libdir = os.path.join(ROOT, "paper_0911_1407_gb300")
+    exe = work / "t"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lplc",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    assert subprocess.run([str(exe)]).returncode == 0
