@@ -76,3 +76,18 @@ def test_gradient_and_hessian_finite_differences():
     fdh = (bias.bias_gradient(s + h * v, q) - bias.bias_gradient(s - h * v, q)) / (2 * h)
     hv = bias.bias_hessvec(s, v, q)
     assert np.max(np.abs(fdh - hv)) <= 1e-6 * np.max(np.abs(hv))
+
+
+def test_hessian_is_symmetric():
+    """B is symmetric (b depends on |k| only), so H = S^-1 + diag(e^s B q)
+    + diag(e^s) B diag(N/u^2) B diag(e^s) is too."""
+    rng = np.random.default_rng(11)
+    n, box = 8, 60.0
+    p = _problem(n, box, rng, True, dc=0.2)
+    kb, b = _bias_table(n, box, 1.2, slope=-0.1)
+    q = bias.BiasProblem(p, bias.bias_multipliers(n, box, kb, b, 1.2))
+    s = 0.2 * rng.standard_normal(p.N.shape)
+    u, v = rng.standard_normal(s.shape), rng.standard_normal(s.shape)
+    a = float(np.sum(u * bias.bias_hessvec(s, v, q)))
+    c = float(np.sum(v * bias.bias_hessvec(s, u, q)))
+    assert abs(a - c) <= 1e-12 * max(abs(a), abs(c))

@@ -92,3 +92,13 @@ def test_correlation_without_the_square_roots(monkeypatch):
     monkeypatch.setattr(stats, "correlation",
                         lambda a, b: float(np.sum(a * b) / (np.sum(a * a) * np.sum(b * b))))
     _fails(ts.test_correlation_and_distance)
+
+
+def test_bias_hessian_without_its_coupling_term(monkeypatch):
+    # drop e^s . B(N/u^2 . B(e^s v)), the term that couples cells through B
+    def bad(s, v, q):
+        e = np.exp(s)
+        u = bias.galaxy_density(s, q)
+        return plc.apply_Sinv(v, q.p.inv_lam) + e * bias.apply_B(q.p.wn - q.p.N / u, q.bk) * v
+    monkeypatch.setattr(bias, "bias_hessvec", bad)
+    _fails(tb.test_gradient_and_hessian_finite_differences)
