@@ -681,6 +681,7 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
         ctx, lambda: ctx.gauss_map(N_dev, None, m.nbar, delta=dg2.zero_(), tol=TOL, cg_chunk=1),
         algorithmic_bytes(n))
     bias_extra(plc, m, N_dev, line)
+    adjoint_extra(plc, line)
     # reconstruction quality against the true field (r and D_Euc, Sec. 4.1.2)
     # and the matter statistics of ln(1 + delta) after 10 Mpc/h smoothing
     d_true = torch.expm1(torch.from_numpy(m.s_true).cuda())
@@ -779,6 +780,51 @@ def bias_extra(plc, m, N_dev, line):
     d = s_bias - s
     out["mixed_vs_fp64"] = {"max_abs": float(d.abs().max()), "rel_l2": float(d.norm() / s.norm())}
     line["bias_map"] = out
+
+
+def adjoint_extra(plc, line):
+    """C4: the MAP and its implicit adjoint at 128^3 (adjoint128): forward
+    solve, plc_map_vjp for a cotangent (one CG solve on H lam = u), and the
+    same through the autograd function MapField (forward + backward)."""
+    import torch
+    from paper_0911_1407_gb300 import autograd, mocks
+    m = mocks.make_mock(mocks.WORKLOADS["adjoint128"])
+    n = m.n
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    N_dev = torch.from_numpy(m.N).cuda()
+    u = torch.randn((n, n, n), dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(2))
+    out = {}
+    for prec in ("mixed", "fp64"):
+        c = plc.Context(n, m.box, prec)
+        c.set_prior(m.k_tab, m.P_tab, m.mu)
+        s = torch.full((n, n, n), m.mu, dtype=torch.float64, device="cuda")
+        c.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL)
+        vtol = 1e-6 if prec == "mixed" else 1e-10
+        c.map_vjp(s, None, m.nbar, u, tol=vtol)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, _, st = c.map_vjp(s, None, m.nbar, u, tol=vtol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[prec] = {"vjp_ms": e0.elapsed_time(e1), "cg_iters": st["cg_iters"],
+                     "rel_residual": st["grad_rel"], "tol": vtol}
+        c.close()
+    # autograd: forward MAP + backward adjoint through torch.autograd
+    c = plc.Context(n, m.box, "mixed")
+    Nf = N_dev.double().requires_grad_(True)
+    lnA = torch.zeros((), dtype=torch.float64, device="cuda", requires_grad=True)
+    for rep in range(2):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s_map = autograd.map_field(Nf, lnA, c, m.k_tab, m.P_tab, m.mu, None, m.nbar, tol=TOL)
+        (s_map * u).sum().backward()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    out["autograd_forward_backward_ms"] = e0.elapsed_time(e1)
+    c.close()
+    line["adjoint128"] = out
 
 
 def batch_extra(plc, line):
