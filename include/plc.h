@@ -278,8 +278,11 @@ plc_status plc_smooth(plc_ctx* ctx, const double* x, double* y, double radius);
  * 1 + delta <= 0}, and moments[4] = {mean, variance (population), skewness
  * m3 / m2^(3/2), excess kurtosis m4 / m2^2 - 3} of x over the cells with
  * 1 + delta > 0 (the paper defers these formulas to earlier work; these are
- * the standard ones).  delta: double field.  Uses the solver work fields as
- * scratch.  Synchronises the stream. */
+ * the standard ones).  delta: double field.  The device-side counts live in
+ * a buffer of 4099 entries that the context allocates on the first call
+ * (any nbins in range fits, whatever the grid size).  nbins outside
+ * 1..4096, a non-finite lo, a width <= 0 or a NULL output give
+ * PLC_ERR_INVALID_ARG with nothing launched.  Synchronises the stream. */
 plc_status plc_log_stats(plc_ctx* ctx, const double* delta, double lo, double width, int nbins,
                          long long* counts, long long* outside, double* moments);
 
@@ -358,8 +361,13 @@ plc_status plc_profile_read(plc_ctx* ctx, plc_kernel_time* out, int cap, int* co
  * capture.  All calls on a device share the array and it keeps the last
  * call's contents (each call rewrites everything it reads, so nothing needs
  * clearing); two calls whose work overlaps on the same GPU, e.g. from
- * different streams, race on it: serialise them.  Enqueued on cuda_stream
- * (NULL = legacy default stream); returns after enqueue. */
+ * different streams, race on it: serialise them.  The cached address dies
+ * with the device's primary context: after a cudaDeviceReset, unload and
+ * reload the library before calling this again on that device.  If a CUDA
+ * error from an earlier, unrelated call is pending on entry, nothing is
+ * launched, PLC_ERR_CUDA is returned and the pending error is left in place
+ * for its owner.  Enqueued on cuda_stream (NULL = legacy default stream);
+ * returns after enqueue. */
 plc_status plc_hessvec_noalloc(int n, double box, const double* k, const double* P,
                                int nk, double inv_lambda_dc, const double* s,
                                const double* w, double nbar, const double* v,

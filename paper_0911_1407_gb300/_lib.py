@@ -220,6 +220,14 @@ class Context:
         self._check(self.lib.plc_set_prior(self._h, k.ctypes.data_as(DP), P.ctypes.data_as(DP),
                                            int(k.size), float(mu), float(inv_lambda_dc)))
         self.mu = float(mu)
+        self._prior = (k.copy(), P.copy(), float(mu), float(inv_lambda_dc))
+
+    def prior_is(self, k, P, mu: float, inv_lambda_dc: float = 0.0) -> bool:
+        """True when the last plc_set_prior on this context had these arguments."""
+        cur = getattr(self, "_prior", None)
+        return (cur is not None and cur[2] == float(mu) and cur[3] == float(inv_lambda_dc)
+                and np.array_equal(cur[0], np.asarray(k, dtype=np.float64))
+                and np.array_equal(cur[1], np.asarray(P, dtype=np.float64)))
 
     def prior_apply(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         out = self.field() if out is None else out

@@ -13,6 +13,10 @@ prior power spectrum (P -> A P).  Its backward pass is the implicit adjoint
 plc_map_vjp: the stationarity condition g(s*) = 0 gives ds*/dN = H^-1 and
 ds*/d ln A = H^-1 S^-1 (s* - mu), so a cotangent u costs one CG solve
 lam = H^-1 u at the converged state (nothing is stored per iteration).
+The forward pass records the prior it solved with (the scaled table, mu and
+the DC inverse eigenvalue); the backward pass puts that prior back on the
+context if another call has changed it since, so several MAP fields taken on
+one context each get the adjoint of their own amplitude.
 """
 from __future__ import annotations
 
@@ -48,33 +52,40 @@ def neg_log_posterior(s: torch.Tensor, ctx: Context, N: torch.Tensor,
 
 
 class MapField(torch.autograd.Function):
-    """s* = MapField.apply(N, ln_amp, ctx, k, P, mu, w, nbar, opts).
+    """s* = MapField.apply(N, ln_amp, ctx, k, P, mu, inv_lambda_dc, w, nbar, opts).
 
     N: float64 counts (whole numbers; cast to int32 for the solve);
-    ln_amp: 0-d float64 tensor, the prior is P(k) e^{ln_amp};
+    ln_amp: 0-d float64 tensor, the prior is P(k) e^{ln_amp} (the DC inverse
+    eigenvalue inv_lambda_dc is not scaled: the amplitude multiplies the
+    non-DC eigenvalues);
     opts: dict of plc_opts fields for both the solve and the adjoint CG.
     """
 
     @staticmethod
     def forward(fctx, N: torch.Tensor, ln_amp: torch.Tensor, ctx: Context, k, P, mu: float,
-                w: Optional[torch.Tensor], nbar: float, opts: dict):
+                inv_lambda_dc: float, w: Optional[torch.Tensor], nbar: float, opts: dict):
         amp = float(torch.exp(ln_amp.detach().double()).item())
-        ctx.set_prior(k, np.asarray(P, dtype=np.float64) * amp, mu)
+        prior = (np.array(k, dtype=np.float64), np.asarray(P, dtype=np.float64) * amp,
+                 float(mu), float(inv_lambda_dc))
+        ctx.set_prior(*prior)
         Ni = N.detach().round().to(torch.int32)
         res = ctx.newton_krylov_map(Ni, w, nbar, **opts)
-        fctx.ctx, fctx.w, fctx.nbar, fctx.opts = ctx, w, nbar, opts
+        fctx.ctx, fctx.w, fctx.nbar, fctx.opts, fctx.prior = ctx, w, nbar, opts, prior
         fctx.save_for_backward(res.s)
         return res.s.clone()
 
     @staticmethod
     def backward(fctx, u: torch.Tensor):
         (s,) = fctx.saved_tensors
+        if not fctx.ctx.prior_is(*fctx.prior):
+            fctx.ctx.set_prior(*fctx.prior)
         vjp_N, vjp_lnA, _ = fctx.ctx.map_vjp(s, fctx.w, fctx.nbar,
                                              u.detach().double().contiguous(), **fctx.opts)
         g_lnA = torch.tensor(vjp_lnA, dtype=torch.float64, device=s.device)
-        return vjp_N, g_lnA, None, None, None, None, None, None, None
+        return vjp_N, g_lnA, None, None, None, None, None, None, None, None
 
 
 def map_field(N: torch.Tensor, ln_amp: torch.Tensor, ctx: Context, k, P, mu: float,
-              w: Optional[torch.Tensor] = None, nbar: float = 1.0, **opts) -> torch.Tensor:
-    return MapField.apply(N, ln_amp, ctx, k, P, mu, w, nbar, opts)
+              w: Optional[torch.Tensor] = None, nbar: float = 1.0, inv_lambda_dc: float = 0.0,
+              **opts) -> torch.Tensor:
+    return MapField.apply(N, ln_amp, ctx, k, P, mu, inv_lambda_dc, w, nbar, opts)

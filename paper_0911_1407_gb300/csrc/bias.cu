@@ -119,7 +119,8 @@ End newton_phase(Fields<T, TC>& F, BSums gs, const plc_opts& o, Progress& P, boo
   plc_ctx* c = F.c;
   for (;;) {
     const double gnorm = std::sqrt(gs.gg);
-    if (!std::isfinite(gnorm) || !std::isfinite(gs.f())) return End::kNonFinite;
+    if (!std::isfinite(gnorm) || !std::isfinite(gs.f()) || !std::isfinite(P.g0))
+      return End::kNonFinite;
     const double rel = P.g0 > 0.0 ? gnorm / P.g0 : 0.0;
     P.S.grad_rel = rel;
     P.S.neg_logpost = gs.f();

@@ -88,7 +88,7 @@ void release(plc_ctx* c) {
   plc::graph_release(c);
   plc::profile_release(c);
   void* ptrs[] = {c->specA, c->specB, c->tw64, c->tw32, c->twff, c->expff, c->M64, c->M32,
-                  c->lk, c->lP, c->sc, c->partials, c->Mb64, c->Mb32, c->lkb, c->lbb};
+                  c->lk, c->lP, c->sc, c->partials, c->Mb64, c->Mb32, c->lkb, c->lbb, c->hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->wf)
@@ -667,13 +667,15 @@ plc_status plc_log_stats(plc_ctx* c, const double* delta, double lo, double widt
   PLC_TRY(need_field(c, delta, "delta", true));
   if (!(width > 0.0) || !std::isfinite(width) || !std::isfinite(lo))
     return fail(c, PLC_ERR_INVALID_ARG, "bins need finite lo and width > 0");
-  if (nbins < 1 || nbins > 4096) return fail(c, PLC_ERR_INVALID_ARG, "nbins must be 1..4096");
+  if (nbins < 1 || nbins > plc_ctx::kMaxBins)
+    return fail(c, PLC_ERR_INVALID_ARG, "nbins must be 1..4096");
   if (!counts || !outside || !moments) return fail(c, PLC_ERR_INVALID_ARG, "NULL output");
   return guarded(c, [&]() -> plc_status {
-    ensure_work_fields(c);
+    // the counts have their own buffer: a work field holds only n^3 entries,
+    // fewer than nbins + 3 on small grids
+    if (!c->hist) dalloc(&c->hist, sizeof(unsigned long long) * (plc_ctx::kMaxBins + 3));
     std::vector<long long> all(nbins + 3);
-    plc::log_stats(c, delta, lo, width, nbins, all.data(), moments,
-                   static_cast<unsigned long long*>(c->wf[12]));
+    plc::log_stats(c, delta, lo, width, nbins, all.data(), moments, c->hist);
     for (int j = 0; j < nbins; ++j) counts[j] = all[j];
     for (int j = 0; j < 3; ++j) outside[j] = all[nbins + j];
     return PLC_OK;

@@ -99,6 +99,11 @@ struct plc_ctx {
   double* partials = nullptr;
   size_t partial_blocks = 0;
 
+  // Histogram counts of plc_log_stats: kMaxBins + 3 entries (below, above,
+  // invalid at the end), allocated on its first call.
+  static constexpr int kMaxBins = 4096;
+  unsigned long long* hist = nullptr;
+
   // Solver work fields, each n^3 doubles, allocated on first use.
   static constexpr int kNumWork = 13;
   void* wf[kNumWork] = {};

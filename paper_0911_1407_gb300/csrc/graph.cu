@@ -122,7 +122,9 @@ __global__ void k_ctl_head(DevCtl* t, const DevScalars* sc, Handle h_switch, int
   t->loops += 1;
   const double gnorm = sqrt(sc->red[2]), f = f_of(sc);
   int sw = 0;
-  if (!isfinite(gnorm) || !isfinite(f)) {
+  // a non-finite g0 (NaN or Inf in the caller's start or in w) would make
+  // every relative norm look converged
+  if (!isfinite(gnorm) || !isfinite(f) || !isfinite(t->g0)) {
     t->stop = 1;
     t->status = PLC_ERR_NONFINITE;
   } else if (t->mixed && !t->fp64) {
@@ -149,7 +151,7 @@ __global__ void k_ctl_decide(DevCtl* t, DevScalars* sc, Handle h_newton, Handle 
   int step = -1;
   if (!t->stop) {
     const double gnorm = sqrt(sc->red[2]), f = f_of(sc);
-    if (!isfinite(gnorm) || !isfinite(f)) {
+    if (!isfinite(gnorm) || !isfinite(f) || !isfinite(t->g0)) {
       t->stop = 1;
       t->status = PLC_ERR_NONFINITE;
     } else {

@@ -13,6 +13,10 @@
 // The array's name is a host-side stand-in in host code, not a device
 // address: the device address is looked up with cudaGetSymbolAddress once
 // per device, on the first call made with that device current, and cached.
+// A cudaDeviceReset (or anything else that destroys and re-creates the
+// device's primary context) reloads the module at a new address, so after
+// one the library must be unloaded and loaded again before this entry point
+// is called on that device.
 #include <mutex>
 #include <string>
 
@@ -41,6 +45,13 @@ constexpr size_t kScratchBytes = kOffM + align256(kMBytes);   // about 4.2 MiB
 // The scratch: two half-spectra, the twiddles and the per-|m|^2 inverse
 // eigenvalues of the largest grid served.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// The passes run with dynamic shared memory below the 48 KB that needs no
+// opt-in attribute (this file sets none): twiddles plus two padded tiles of
+// the largest line length.
+static_assert(sizeof(double2) * (kNoAllocMaxN + 2 * (size_t)kNoAllocMaxN * plc::PassGeom<double>::P) <=
+                  48 * 1024,
+              "FP64 Stockham tiles of the largest grid must fit the default shared-memory limit");
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -168,8 +179,15 @@ extern "C" plc_status plc_hessvec_noalloc(int n, double box, const double* k, co
   if (w && (reinterpret_cast<uintptr_t>(w) & 15u))
     return fail("plc_hessvec_noalloc: w must be 16-byte aligned");
 
+  // An error left pending by an earlier, unrelated call would be reported
+  // (and cleared) by the launch check below as if it were this call's:
+  // refuse to run while one is pending, and leave it for its owner.
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return fail(std::string("plc_hessvec_noalloc: a CUDA error is pending from an earlier call "
+                            "(not cleared): ") + cudaGetErrorString(e), PLC_ERR_CUDA);
   unsigned char* base = nullptr;
-  cudaError_t e = scratch_address(&base);
+  e = scratch_address(&base);
   if (e != cudaSuccess)
     return fail(std::string("plc_hessvec_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e),
                 PLC_ERR_CUDA);

@@ -4,8 +4,11 @@
 // epilogues (fused into the last pass) turn y = S^-1 x into the gradient or a
 // Hessian-vector product and accumulate the dot products the solver needs;
 // finalizers run once on the grid totals.  Element-wise kernels cover the CG
-// recurrences and set-up work.  All reductions are in FP64 whatever the
-// field type.
+// recurrences and set-up work.  Reductions accumulate per thread in the
+// field's own precision made compensated (Kahan pairs for FP32 fields,
+// float-float for the float-float transforms, plain FP64 for FP64 fields),
+// merge across lanes and warps in that arithmetic, and go to FP64 once per
+// block; the block totals are summed in FP64 in block order.
 #pragma once
 
 #include "common.cuh"

@@ -238,7 +238,12 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
   double prev_rel = 1.0;
   for (;;) {
     const double gnorm = std::sqrt(gs.gg);
-    if (!std::isfinite(gnorm) || !std::isfinite(gs.f())) { status = PLC_ERR_NONFINITE; break; }
+    // a non-finite g0 (NaN or Inf in the caller's start or in w) would make
+    // every relative norm look converged
+    if (!std::isfinite(gnorm) || !std::isfinite(gs.f()) || !std::isfinite(g0)) {
+      status = PLC_ERR_NONFINITE;
+      break;
+    }
     const double rel = g0 > 0.0 ? gnorm / g0 : 0.0;
     S.grad_rel = rel;
     S.neg_logpost = gs.f();

@@ -102,3 +102,45 @@ def test_map_field_amplitude_central_difference(plc):
         vals.append(float((sa * u).sum()))
     fd = (vals[0] - vals[1]) / (2 * h)
     assert abs(ln_amp.grad.item() - fd) <= 1e-5 * abs(fd)
+
+
+def test_map_field_two_amplitudes_on_one_context(plc):
+    """Two MAP fields at different ln A taken on one context, then one
+    backward of their sum: each gets the adjoint of its own prior (the
+    second forward rescales the context's prior; the first backward must
+    restore its own).  Against the oracle's VJP at each amplitude."""
+    from paper_0911_1407_gb300.autograd import map_field
+    m = mocks.make_mock(mocks.WORKLOADS["adjoint32"])
+    rng = np.random.default_rng(11)
+    u1, u2 = rng.standard_normal(m.N.shape), rng.standard_normal(m.N.shape)
+    c = plc.Context(m.n, m.box, "fp64")
+    outs = []
+    for ln_a, u in ((0.3, u1), (-0.4, u2)):
+        N = dev(m.N, torch.float64).requires_grad_(True)
+        la = torch.tensor(ln_a, dtype=torch.float64, device="cuda", requires_grad=True)
+        s = map_field(N, la, c, m.k_tab, m.P_tab, m.mu, None, m.nbar, tol=1e-13)
+        outs.append((N, la, s, u, ln_a))
+    sum((s * dev(u, torch.float64)).sum() for _, _, s, u, _ in outs).backward()
+    for N, la, s, u, ln_a in outs:
+        p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab * np.exp(ln_a))
+        ref = orc.newton_krylov_map(p, tol=1e-13)
+        assert np.max(np.abs(host(s) - ref.s) / np.maximum(np.abs(ref.s), 1)) <= 1e-10
+        lam_ref, lnA_ref, _ = orc.map_vjp(ref.s, u, p, rtol=1e-13)
+        assert np.max(np.abs(host(N.grad) - lam_ref)) <= 1e-9 * np.max(np.abs(lam_ref))
+        assert abs(la.grad.item() - lnA_ref) <= 1e-9 * abs(lnA_ref)
+
+
+def test_map_field_keeps_the_callers_dc_prior(plc):
+    """inv_lambda_dc passes through the forward solve unscaled (the
+    amplitude multiplies the non-DC eigenvalues only)."""
+    from paper_0911_1407_gb300.autograd import map_field
+    m = mocks.make_mock(mocks.WORKLOADS["adjoint32"])
+    dc, ln_a = 0.05, 0.2
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab * np.exp(ln_a),
+                         inv_lambda_dc=dc)
+    ref = orc.newton_krylov_map(p, tol=1e-13)
+    c = plc.Context(m.n, m.box, "fp64")
+    la = torch.tensor(ln_a, dtype=torch.float64, device="cuda")
+    s = map_field(dev(m.N, torch.float64), la, c, m.k_tab, m.P_tab, m.mu, None, m.nbar,
+                  inv_lambda_dc=dc, tol=1e-13)
+    assert np.max(np.abs(host(s) - ref.s) / np.maximum(np.abs(ref.s), 1)) <= 1e-10

@@ -65,6 +65,32 @@ def test_single_mode_eigenvalue(plc, n, mode):
     assert np.max(np.abs(out - lam_inv * f)) <= 1e-12 * lam_inv
 
 
+@pytest.mark.parametrize("alpha1,alpha2", [(-1.7, 0.6), (1.0, -2.4)])
+@pytest.mark.parametrize("n,mode_lo,mode_hi", [(12, (1, 2, 0), (3, 1, 4)), (24, (3, 2, 5), (9, 4, 7)),
+                                               (32, (4, 1, 6), (13, 5, 9))])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_mode_between_table_nodes(plc, n, mode_lo, mode_hi, alpha1, alpha2, precision):
+    """P(k) between table nodes (linear in (ln k, ln P)): a broken power law
+    with its kink on a node makes the eigenvalue of an off-node mode exact,
+    on both sides of the kink.  FP64 to 1e-12.  FP32 fields to 2e-5 of the
+    peak element: the transforms' rounding (eps32 = 6e-8 times ~log2(n^3)
+    = 15 stages) leaks into other modes, whose 1/lambda is up to ~10 times
+    the mode's own for these tables."""
+    from tests.test_oracle_operators import _kmag, broken_power_law_table
+    box = 100.0
+    k_lo, k_hi = _kmag(n, box, mode_lo), _kmag(n, box, mode_hi)
+    k, P, P_lo, P_hi = broken_power_law_table(n, box, k_lo, k_hi, alpha1, alpha2)
+    c = plc.Context(n, box, precision)
+    c.set_prior(k, P, 0.0)
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    for mode, Pq in ((mode_lo, P_lo), (mode_hi, P_hi)):
+        f = np.cos(2 * np.pi * (mode[0] * z + mode[1] * y + mode[2] * x) / n - 0.7)
+        ref = f * box ** 3 / (Pq * n ** 3)
+        out = host(c.prior_apply(dev(f, c.real))).astype(np.float64)
+        bar = 1e-12 if precision == "fp64" else 2e-5
+        assert np.max(np.abs(out - ref)) <= bar * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("n,selection", [(8, "uniform"), (24, "radial_masked"), (48, "uniform")])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_logpost_grad(plc, n, selection, precision):

@@ -80,3 +80,32 @@ def test_reconstruction_quality_on_the_production_mock(plc):
     assert abs(r - stats.correlation(a, b)) <= 1e-12
     assert abs(d - stats.euclidean_distance(a, b)) <= 1e-12 * d
     assert 0.0 < r < 1.0
+
+
+@pytest.mark.parametrize("n,nbins", [(4, 4096), (4, 61), (8, 4096)])
+def test_log_stats_many_bins_on_small_grids(plc, n, nbins):
+    """More bins than cells: the device counts have their own 4099-entry
+    buffer, so any nbins up to 4096 is valid on any grid."""
+    rng = np.random.default_rng(nbins + n)
+    lo, width = -3.0, 6.0 / nbins
+    j = rng.integers(-2, nbins + 2, size=n ** 3)
+    xv = lo + (j + 0.5 + 0.3 * rng.uniform(-1, 1, size=n ** 3)) * width
+    delta = (np.exp(xv) - 1.0).reshape(n, n, n)
+    delta[0, 0, 0] = -2.0                              # one invalid cell
+    counts, below, above, invalid, mean, var, skew, kurt = stats.log_density_stats(delta, lo, width, nbins)
+    c = plc.Context(n, 5.0 * n, "fp64")
+    g_counts, g_out, g_mom = c.log_stats(dev(delta, torch.float64), lo, width, nbins)
+    assert np.array_equal(g_counts, counts)
+    assert g_out == (below, above, invalid)
+    for a, b in zip(g_mom, (mean, var, skew, kurt)):
+        assert abs(a - b) <= 1e-12 * max(abs(b), 1.0)
+
+
+def test_log_stats_rejects_too_many_bins(plc):
+    """nbins beyond 4096 is refused on the host before any launch."""
+    c = plc.Context(4, 20.0, "fp64")
+    delta = torch.zeros((4, 4, 4), dtype=torch.float64, device="cuda")
+    for nbins in (0, 4097):
+        with pytest.raises(plc.PlcError) as e:
+            c.log_stats(delta, -1.0, 0.1, nbins)
+        assert e.value.status == 1

@@ -2,6 +2,9 @@
 
 * S^-1 on a single Fourier mode is a scalar multiple 1/lambda_k (Sec. 2.2),
   with lambda_k = P(|k|) n^3 / L^3 read straight off a table node.
+* Between table nodes P is linear in (ln k, ln P), which is exact for a
+  power law: a broken power law with its kink on a node gives the
+  eigenvalue of an off-node mode in closed form, on either side of the kink.
 * The gradient (Sec. 3.1.2) is the derivative of the objective (prior of
   Sec. 2.3 plus likelihood of Sec. 2.1): central finite differences.
 * The Hessian (Sec. 3.1.2) is the derivative of the gradient, symmetric and
@@ -40,6 +43,49 @@ def test_single_mode_eigenvalue(n, mode):
     lam = Pq * n ** 3 / box ** 3
     out = plc.apply_Sinv(field, inv)
     assert np.max(np.abs(out - field / lam)) < 1e-12 * np.max(np.abs(field / lam))
+
+
+def broken_power_law_table(n, box, k_lo, k_hi, alpha1, alpha2, A=50.0):
+    """Table of P = A (k/k_b)^alpha1 below k_b and A (k/k_b)^alpha2 above it,
+    k_b = sqrt(k_lo k_hi), on log nodes k_b e^{j h} with h = 0.8 ln(k_hi/k_lo):
+    k_lo and k_hi then sit strictly inside the two segments next to the kink,
+    at fractions 0.375 and 0.625 of a segment.  Returns the table and the
+    exact P at k_lo and k_hi."""
+    kb = math.sqrt(k_lo * k_hi)
+    h = 0.8 * math.log(k_hi / k_lo)
+    kmin, kmax = 0.5 * 2 * math.pi / box, 1.01 * math.sqrt(3) * math.pi * n / box
+    j = np.arange(math.floor(math.log(kmin / kb) / h), math.ceil(math.log(kmax / kb) / h) + 1)
+    k = kb * np.exp(h * j)
+
+    def P(x):
+        return A * (x / kb) ** np.where(x < kb, alpha1, alpha2)
+    return k, P(k), float(P(np.array(k_lo))), float(P(np.array(k_hi)))
+
+
+def _kmag(n, box, mode):
+    ms = [m if m <= n // 2 else m - n for m in mode]
+    return 2 * math.pi / box * math.sqrt(sum(m * m for m in ms))
+
+
+@pytest.mark.parametrize("alpha1,alpha2", [(-1.7, 0.6), (1.0, -2.4), (0.5, 0.5)])
+@pytest.mark.parametrize("n,mode_lo,mode_hi", [(8, (0, 1, 1), (2, 1, 2)), (12, (1, 2, 0), (3, 1, 4)),
+                                               (16, (2, 3, 5), (7, 1, 6))])
+def test_single_mode_between_table_nodes(n, mode_lo, mode_hi, alpha1, alpha2):
+    box = 100.0
+    k_lo, k_hi = _kmag(n, box, mode_lo), _kmag(n, box, mode_hi)
+    k_tab, P_tab, P_lo, P_hi = broken_power_law_table(n, box, k_lo, k_hi, alpha1, alpha2)
+    # both modes lie strictly between nodes (at least 1/4 of a segment away)
+    lk = np.log(k_tab)
+    for kq in (k_lo, k_hi):
+        gap = np.min(np.abs(lk - math.log(kq))) / (lk[1] - lk[0])
+        assert gap > 0.25
+    inv = plc.inverse_eigenvalues(n, box, k_tab, P_tab)
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    for mode, Pq in ((mode_lo, P_lo), (mode_hi, P_hi)):
+        f = np.cos(2 * np.pi * (mode[0] * z + mode[1] * y + mode[2] * x) / n - 0.7)
+        ref = f * box ** 3 / (Pq * n ** 3)
+        out = plc.apply_Sinv(f, inv)
+        assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
 def test_dc_rule():

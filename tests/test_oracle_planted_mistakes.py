@@ -102,3 +102,27 @@ def test_bias_hessian_without_its_coupling_term(monkeypatch):
         return plc.apply_Sinv(v, q.p.inv_lam) + e * bias.apply_B(q.p.wn - q.p.N / u, q.bk) * v
     monkeypatch.setattr(bias, "bias_hessvec", bad)
     _fails(tb.test_gradient_and_hessian_finite_differences)
+
+
+def _interp_linear_in_k(k, k_tab, P_tab):
+    """P linear in k between nodes (instead of linear in (ln k, ln P))."""
+    return np.interp(k, k_tab, P_tab)
+
+
+def _interp_log_p_linear_in_k(k, k_tab, P_tab):
+    """ln P linear in k between nodes."""
+    return np.exp(np.interp(k, k_tab, np.log(P_tab)))
+
+
+def _interp_wrong_segment(k, k_tab, P_tab):
+    """The right formula on the segment to the left of the right one."""
+    k_tab, P_tab, k = (np.asarray(a, dtype=np.float64) for a in (k_tab, P_tab, k))
+    j = np.clip(np.searchsorted(k_tab, k, side="right") - 2, 0, k_tab.size - 2)
+    t = (np.log(k) - np.log(k_tab[j])) / (np.log(k_tab[j + 1]) - np.log(k_tab[j]))
+    return np.exp(np.log(P_tab[j]) + t * (np.log(P_tab[j + 1]) - np.log(P_tab[j])))
+
+
+@pytest.mark.parametrize("bad", [_interp_linear_in_k, _interp_log_p_linear_in_k, _interp_wrong_segment])
+def test_pk_interpolation_mistakes(monkeypatch, bad):
+    monkeypatch.setattr(plc, "interp_pk", bad)
+    _fails(lambda: to.test_single_mode_between_table_nodes(12, (1, 2, 0), (3, 1, 4), -1.7, 0.6))
