@@ -17,8 +17,13 @@ second (FP32, FP64), per-kernel device time and the roofline of the
 dominant kernel, and the FP64 CPU oracle timed on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl plc|reference]
+    python bench.py --cpu-full [--out FILE]
 
 With --impl reference the FP64 CPU oracle is timed instead (rank 0 only).
+--cpu-full times whole oracle solves on the host cores (minutes: the 256^3
+solve alone takes several) and measures the mixed-precision GPU MAP against
+the oracle's MAP converged to 1e-12; its record, committed under profiles/,
+is quoted in the default line with the sources it was taken on.
 """
 from __future__ import annotations
 
@@ -208,6 +213,128 @@ def load_traffic(n: int):
 # ----------------------------------------------------------------------------
 # the oracle on the host cores
 # ----------------------------------------------------------------------------
+CPU_RECORD = os.path.join(ROOT, "profiles", "cpu_baseline_oracle.json")
+
+
+def oracle_hash() -> str:
+    """Hash of the oracle's sources (the CPU baseline is the oracle as it stands)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "oracle", "*.py"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def time_oracle_map(spec, warmup: int, reps: int, tol: float = TOL):
+    """Whole oracle MAP solves of one workload, s^0 = mu to ||g|| / ||g0|| < tol:
+    `warmup` untimed, then `reps` timed; returns the mock, the problem, the
+    last result and the timed seconds."""
+    from oracle import plc as orc
+    from paper_0911_1407_gb300 import mocks
+    m = mocks.make_mock(spec)
+    p = orc.make_problem(m.N, m.w, m.nbar, m.mu, m.n, m.box, m.k_tab, m.P_tab)
+    r, times = None, []
+    for k in range(warmup + reps):
+        t0 = time.perf_counter()
+        r = orc.newton_krylov_map(p, tol=tol)
+        if k >= warmup:
+            times.append(time.perf_counter() - t0)
+    return m, p, r, times
+
+
+def batch_spec_of_size(n: int):
+    from paper_0911_1407_gb300 import mocks
+    return next(sp for sp in mocks.batch_specs() if sp.n == n)
+
+
+def timing_entry(name, m, r, times, warmup):
+    return {"workload": name, "n": m.n, "seconds": statistics.median(times),
+            "maps_per_s": 1.0 / statistics.median(times), "runs": len(times), "warmup": warmup,
+            "newton_iters": r.newton_iters, "cg_iters": r.cg_iters, "grad_rel": r.grad_rel}
+
+
+def cpu_full(args):
+    """Whole oracle solves on the host cores and the mixed GPU MAP against the
+    oracle's MAP at 1e-12 (selection128, production256); one JSON record."""
+    import torch
+    from paper_0911_1407_gb300 import build
+    build.build()
+    import paper_0911_1407_gb300 as plc
+    from paper_0911_1407_gb300 import mocks
+    from oracle import plc as orc
+    torch.cuda.set_device(0)
+    rec = {"csrc": build.source_hash(), "oracle": oracle_hash(), "cores": os.cpu_count(),
+           "cpu_model": cpu_model(), "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "tol": TOL, "timing": "time.perf_counter around oracle.plc.newton_krylov_map, "
+                                 "s^0 = mu, median of the timed runs", "time_to_map": [],
+           "mixed_vs_oracle": {}}
+    plan = [("C1 plain32", mocks.WORKLOADS["plain32"], 1, 3),
+            ("C5 64^3 (batch mock)", batch_spec_of_size(64), 1, 3),
+            ("C5 96^3 (batch mock)", batch_spec_of_size(96), 1, 3),
+            ("C5 128^3 (batch mock)", batch_spec_of_size(128), 0, 3),
+            ("C2 selection128", mocks.WORKLOADS["selection128"], 0, 3),
+            ("C3 production256", mocks.WORKLOADS["production256"], 0, 1)]
+    finals = {}
+    for name, spec, warm, reps in plan:
+        m, p, r, times = time_oracle_map(spec, warm, reps)
+        rec["time_to_map"].append(timing_entry(name, m, r, times, warm))
+        print(json.dumps(rec["time_to_map"][-1]), flush=True)
+        if spec.name in ("selection128", "production256"):
+            finals[spec.name] = (m, p, r)
+    for key, (m, p, r) in finals.items():
+        # the oracle continued from its 1e-6 iterate to 1e-12 (same g0: the
+        # minimiser is unique, so the path does not matter)
+        t0 = time.perf_counter()
+        ref = orc.newton_krylov_map(p, s0=r.s, g0_norm=r.g0_norm, tol=1e-12)
+        t_more = time.perf_counter() - t0
+        c = plc.Context(m.n, m.box, "mixed")
+        c.set_prior(m.k_tab, m.P_tab, m.mu)
+        w = None if m.w is None else torch.from_numpy(m.w).cuda()
+        res = c.newton_krylov_map(torch.from_numpy(m.N).cuda(), w, m.nbar, tol=TOL)
+        s_gpu = res.s.cpu().numpy()
+        d = s_gpu - ref.s
+        rec["mixed_vs_oracle"][key] = {
+            "max_abs": float(np.max(np.abs(d))),
+            "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref.s)),
+            "gpu_grad_rel": res.stats["grad_rel"], "oracle_grad_rel": ref.grad_rel,
+            "oracle_converged": bool(ref.converged),
+            "oracle_newton_iters_past_1e-6": ref.newton_iters, "oracle_seconds_past_1e-6": t_more}
+        print(json.dumps({key: rec["mixed_vs_oracle"][key]}), flush=True)
+        c.close()
+    out = args.out or os.path.join(ROOT, "gpurun_out", "cpu_full.json")
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
+def cpu_record():
+    """The committed --cpu-full record, with whether it matches the sources."""
+    if not os.path.exists(CPU_RECORD):
+        return None
+    from paper_0911_1407_gb300 import build
+    rec = json.load(open(CPU_RECORD))
+    rec["matches_current_csrc"] = rec.get("csrc") == build.source_hash()
+    rec["matches_current_oracle"] = rec.get("oracle") == oracle_hash()
+    rec["source"] = "profiles/cpu_baseline_oracle.json (python bench.py --cpu-full)"
+    return rec
+
+
 def time_oracle_sample(m, repeats: int = 1):
     """One oracle Hessian-vector product and one gradient at full size."""
     from oracle import plc as orc
@@ -249,9 +376,15 @@ def reference_arm(args):
             "config": workload_config(args.gpus),
             "precision": "FP64 throughout (the oracle)",
             "cpu_baseline": {"value": 1.0 / t_map, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": 1.0 / t_map, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    rec = cpu_record()
+    if rec is not None:
+        # whole oracle solves measured by --cpu-full, beside the modelled figure
+        line["cpu_baseline"]["measured_full"] = {
+            k: rec.get(k) for k in ("time_to_map", "cores", "cpu_model", "when", "oracle",
+                                    "matches_current_oracle", "source")}
     print(json.dumps(line), flush=True)
 
 
@@ -307,9 +440,15 @@ def main(argv=None):
                          "(same kernels; for profilers that cannot see into conditional graphs)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time whole oracle solves on the host cores and the mixed GPU MAP "
+                         "against the oracle at 1e-12; writes one JSON record (minutes)")
+    ap.add_argument("--out", help="file for the --cpu-full record")
     args = ap.parse_args(argv)
     if args.micro:
         return micro(args)
+    if args.cpu_full:
+        return cpu_full(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -723,11 +862,37 @@ def extras(plc, m, ctx, s_mixed, N_dev, line, args):
         # the oracle's own iteration on this workload (as the reference arm)
         hvc, gc = REF_HV_PER_MAP, REF_GRAD_PER_MAP
         t_map = t_hv * hvc + t_g * gc
+        # whole oracle solves that fit the bounded budget, measured here:
+        # C1 (32^3) and one 64^3 batch mock, median of 3 after 1 warm-up
+        measured = []
+        for name, spec in (("C1 plain32", mocks_mod().WORKLOADS["plain32"]),
+                           ("C5 64^3 (batch mock)", batch_spec_of_size(64))):
+            mm, _, rr, times = time_oracle_map(spec, 1, 3)
+            measured.append(timing_entry(name, mm, rr, times, 1))
         line["cpu_baseline"] = {
             "value": 1.0 / t_map, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one oracle Hv ({t_hv:.2f} s) and one gradient+objective ({t_g:.2f} s) at "
-                       f"256^3, scaled to the oracle's {hvc} Hv and {gc} gradients per MAP"),
-            "hv_per_s": 1.0 / t_hv}
+            "cpu_model": cpu_model(),
+            "sample": (f"modelled: one oracle Hv ({t_hv:.2f} s) and one gradient+objective "
+                       f"({t_g:.2f} s) at 256^3, scaled to the oracle's {hvc} Hv and {gc} "
+                       f"gradients per MAP; measured: whole oracle solves of C1 and a 64^3 "
+                       f"mock in this run (measured_here), and of every config in the "
+                       f"committed --cpu-full record (measured_full)"),
+            "hv_per_s": 1.0 / t_hv, "measured_here": measured}
+        rec = cpu_record()
+        if rec is not None:
+            line["cpu_baseline"]["measured_full"] = {
+                k: rec.get(k) for k in ("time_to_map", "cores", "cpu_model", "when", "oracle",
+                                        "matches_current_oracle", "source")}
+    rec = cpu_record()
+    if rec is not None:
+        line["mixed_vs_oracle"] = {**rec.get("mixed_vs_oracle", {}), "csrc": rec.get("csrc"),
+                                   "matches_current_csrc": rec["matches_current_csrc"],
+                                   "source": rec["source"]}
+
+
+def mocks_mod():
+    from paper_0911_1407_gb300 import mocks
+    return mocks
 
 
 def bias_extra(plc, m, N_dev, line):

@@ -38,3 +38,8 @@ def small_mock(n, selection="uniform", sigma=1.0, nbar=2.0, box=None, seed=1):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def max_rel(a, b):
+    """Largest element-wise error over the reference's largest element."""
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))

@@ -1,7 +1,11 @@
 """GPU parity of the LSQ-Wiener filter (plc_wiener_lsq) against the oracle.
 
-Bars: FP64 relative L2 <= 1e-10 of the oracle's solution (both to relative
-residual 1e-12); PLC_MIXED (FP32 CG) relative L2 <= 1e-5 at residual 1e-6.
+Bars: FP64 every element within 1e-10 of the solution's largest element,
+and relative L2 <= 1e-10, of the oracle's solution (both to relative
+residual 1e-12: the error is the residual times the inverse operator's
+norm, a few hundred here); PLC_MIXED (FP32 CG) relative L2 <= 1e-5 and
+every element within 5e-5 of the largest at residual 1e-6 (the same
+argument at 1e-6 plus the FP32 rounding of the iterate).
 At the full workload sizes the GPU solution's residual is taken with the
 oracle's own FP64 operator.
 """
@@ -13,7 +17,7 @@ import torch
 
 from oracle import filters, plc as orc
 from paper_0911_1407_gb300 import mocks
-from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock
+from tests.gpu_util import dev, ensure_lib, host, max_rel, rel_l2, small_mock
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +48,7 @@ def test_lsq_matches_oracle(plc, n, sel, precision):
     d, st, stats = c.wiener_lsq(dev(m.N, torch.int32), dev(m.w, torch.float64), m.nbar, tol=tol)
     assert st == 0 and stats["grad_rel"] <= tol
     assert rel_l2(host(d), ref) <= (1e-10 if precision == "fp64" else 1e-5)
+    assert max_rel(host(d), ref) <= (1e-10 if precision == "fp64" else 5e-5)
 
 
 def test_lsq_diagonal_prior_closed_form(plc):

@@ -13,7 +13,7 @@ import torch
 
 from oracle import plc as orc
 from paper_0911_1407_gb300 import mocks
-from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock
+from tests.gpu_util import dev, ensure_lib, host, max_rel, rel_l2, small_mock
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def _gpu_map(plc, m, precision, tol, **kw):
     return host(r.s), r.stats
 
 
-@pytest.mark.parametrize("key", ["plain32", "sel24"])
+@pytest.mark.parametrize("key", ["plain32", "sel24", "sel48"])
 def test_map_fp64_matches_oracle(plc, key):
     m = _mock(key)
     p, ref = _oracle_map(key, m)
@@ -116,6 +116,7 @@ def test_vjp_matches_oracle(plc, precision, bar):
     tol = 1e-13 if precision == "fp64" else 1e-6
     vN, vA, st = c.map_vjp(dev(ref.s, torch.float64), None, m.nbar, dev(u, torch.float64), tol=tol)
     assert rel_l2(host(vN), lam_ref) <= bar
+    assert max_rel(host(vN), lam_ref) <= bar
     assert abs(vA - lnA_ref) <= bar * abs(lnA_ref)
 
 

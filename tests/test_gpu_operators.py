@@ -6,10 +6,14 @@ tiles along z, y and the n/2+1 kx lines; n = 4 and 6 are smaller than one
 tile; n = 6, 18 and 54 (one factor of 2) take the one-element-per-step x
 passes, the others the 4-wide ones; n = 32, 64, 96, 128, 192, 256 use the
 four-step FP32 transforms.  FP64 bar: relative error <= 1e-12 (an FFT round trip
-of length n^3 in double accumulates a few 1e-15 per stage).  FP32 bar
-(PLC_MIXED operators): relative L2 <= 1e-5, from eps32 = 6e-8 times the
-~log2(n^3) <= 27 butterfly stages of the two transforms and the pointwise
-tail, with margin.
+of length n^3 in double accumulates a few 1e-15 per stage).  FP32 bars
+(PLC_MIXED operators), element by element and as a norm: every element
+within 2e-5 of the reference's largest element, and relative L2 <= 1e-5.
+Each output element is a sum over all n^3 inputs through ~log2(n^3) <= 27
+butterfly stages per transform, two transforms, with rounding eps32 = 6e-8
+per stage: ~2 x 27 x 6e-8 = 3.2e-6 of the transformed field's scale in the
+worst case, times the spread of the multiplier 1/lambda across the modes
+that carry the field (a few), plus the pointwise tail's rounding.
 """
 import math
 
@@ -18,7 +22,9 @@ import pytest
 import torch
 
 from oracle import plc as orc
-from tests.gpu_util import dev, ensure_lib, host, rel_l2, small_mock, pk_table_for
+from tests.gpu_util import dev, ensure_lib, host, max_rel, rel_l2, small_mock, pk_table_for
+
+FP32_MAX = 2e-5     # element-wise bar of the FP32 operators (module docstring)
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +57,7 @@ def test_prior_apply(plc, n, precision):
         assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
     else:
         assert rel_l2(y, ref) <= 1e-5
+        assert max_rel(y, ref) <= FP32_MAX
 
 
 @pytest.mark.parametrize("n,mode", [(32, (0, 0, 1)), (32, (16, 3, 7)), (24, (12, 12, 12)),
@@ -111,7 +118,9 @@ def test_logpost_grad(plc, n, selection, precision):
         # s itself is rounded to FP32: compare with the oracle at the rounded s
         s32 = s.astype(np.float32).astype(np.float64)
         assert abs(f - orc.neg_log_posterior(s32, p)) <= 1e-6 * abs(f_ref)
-        assert rel_l2(g, orc.gradient(s32, p)) <= 1e-5
+        g_ref32 = orc.gradient(s32, p)
+        assert rel_l2(g, g_ref32) <= 1e-5
+        assert max_rel(g, g_ref32) <= FP32_MAX
 
 
 @pytest.mark.parametrize("n", [6, 24, 48, 96])
@@ -132,6 +141,7 @@ def test_hessvec(plc, n, precision):
         assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
     else:
         assert rel_l2(out, ref) <= 1e-5
+        assert max_rel(out, ref) <= FP32_MAX
 
 
 def test_hessian_symmetric_and_pd_on_gpu(plc):
@@ -211,3 +221,5 @@ def test_operators_at_production_sizes(plc, n, precision):
     else:
         assert rel_l2(y, r["sinv"]) <= 1e-5
         assert rel_l2(hv, r["hv32"]) <= 1e-5
+        assert max_rel(y, r["sinv"]) <= FP32_MAX
+        assert max_rel(hv, r["hv32"]) <= FP32_MAX

@@ -3,19 +3,25 @@ offered factor order, and the shared-memory Stockham stages) computes the
 same operators, and the autotuner picks one of them.
 
 The schedules offered per n are those of the library's table (ctx.h,
-kFourStep); FP32 bar as in test_gpu_operators: relative L2 <= 1e-5.
+kFourStep); lengths without a four-step form (24, 48, 54: ragged tiles)
+run the Stockham stages only.  FP32 bars as in test_gpu_operators: every
+element within 2e-5 of the reference's largest, relative L2 <= 1e-5.
 """
 import numpy as np
 import pytest
 import torch
 
 from oracle import plc as orc
-from tests.gpu_util import dev, ensure_lib, host, rel_l2, pk_table_for
+from tests.gpu_util import dev, ensure_lib, host, max_rel, rel_l2, pk_table_for
 
 pytestmark = pytest.mark.gpu
 
 OFFERED = {256: [(16, 16)], 192: [(16, 12), (12, 16)], 128: [(16, 8), (8, 16)],
-           96: [(12, 8), (8, 12)], 64: [(8, 8)], 32: [(8, 4)]}
+           96: [(12, 8), (8, 12)], 64: [(8, 8)], 32: [(8, 4)], 24: [], 48: [], 54: []}
+
+
+def _close(out, ref):
+    return rel_l2(out, ref) <= 1e-5 and max_rel(out, ref) <= 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -23,7 +29,7 @@ def plc():
     return ensure_lib()
 
 
-@pytest.mark.parametrize("n", [32, 64, 96, 128, 192])
+@pytest.mark.parametrize("n", [24, 32, 48, 54, 64, 96, 128, 192])
 def test_every_schedule_matches_the_oracle(plc, n):
     box, mu, nbar = 6.0 * n, -0.4, 1.3
     k, P = pk_table_for(n, box, seed=n)
@@ -42,13 +48,13 @@ def test_every_schedule_matches_the_oracle(plc, n):
     xs, ss, vs, Nd = dev(x, torch.float32), dev(s, torch.float32), dev(v, torch.float32), dev(N, torch.int32)
     for f1, f2 in [(0, 0)] + OFFERED[n]:
         c.set_fft_schedule(f1, f2)
-        assert rel_l2(host(c.prior_apply(xs)), ref_y) <= 1e-5, (f1, f2)
-        assert rel_l2(host(c.hessvec(ss, None, nbar, vs)), ref_hv) <= 1e-5, (f1, f2)
+        assert _close(host(c.prior_apply(xs)), ref_y), (f1, f2)
+        assert _close(host(c.hessvec(ss, None, nbar, vs)), ref_hv), (f1, f2)
         _, g = c.logpost_grad(ss, Nd, None, nbar)
-        assert rel_l2(host(g), ref_g) <= 1e-5, (f1, f2)
+        assert _close(host(g), ref_g), (f1, f2)
     f1, f2, us = c.autotune(reps=5)
     assert (f1, f2) in [(0, 0)] + OFFERED[n] and us > 0.0
-    assert rel_l2(host(c.prior_apply(xs)), ref_y) <= 1e-5
+    assert _close(host(c.prior_apply(xs)), ref_y)
 
 
 def test_schedule_validation(plc):
