@@ -143,6 +143,11 @@ template <typename T, typename TS, typename TC>
 void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar, T* y,
                  T* g, TC* D, TC* r, bool jac);
 // Newton trial point s + tau xi without an FFT (see k_newton_update).
+// The sums of the FP64 gradient of the mixed solve at s (float-float
+// transforms, no field stored) into sc->red; false when the length has no
+// four-step schedule (nothing launched).
+bool grad_sums_ff(plc_ctx* c, const double* s, const double* w, const int32_t* N, double nbar,
+                  bool jac);
 template <typename T, typename TC>
 void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,

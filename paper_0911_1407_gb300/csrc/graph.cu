@@ -52,6 +52,7 @@ struct DevCtl {
   // state
   double g0, prev_rel, f0, xg, scale, eps;
   int it, q, par, fp64, stop, status, loops, cg_count;
+  int check;   // the FP32 gradient passed the stopping test at the switch
   // statistics
   long long cg_iters, grad_evals, grad_ffts, grad_ffts_fp64, kernels;
   double grad_rel, neg_logpost;
@@ -131,14 +132,37 @@ __global__ void k_ctl_head(DevCtl* t, const DevScalars* sc, Handle h_switch, int
     const double rel = t->g0 > 0.0 ? gnorm / t->g0 : 0.0;
     sw = (rel < t->mixed_switch || rel < t->tol ||
           (t->it > 0 && rel < 1e-3 && rel > 0.5 * t->prev_rel)) ? 1 : 0;
+    t->check = rel < t->tol ? 1 : 0;
   }
   cudaGraphSetConditional(h_switch, sw);
 }
 
-__global__ void k_ctl_switched(DevCtl* t, int nk) {
+__global__ void k_ctl_switched(DevCtl* t, int nk, int count_grad) {
   t->kernels += nk;
   t->fp64 = 1;
   t->par = 0;
+  t->grad_evals += count_grad;
+  t->grad_ffts += count_grad;
+  t->grad_ffts_fp64 += count_grad;
+}
+
+// After the FP64 gradient's sums alone (the switch's check): its fields are
+// needed, and the full gradient runs, unless the FP32 gradient passed the
+// stopping test and these sums pass it too (the decision kernel then ends
+// the solve on the same sums).
+__global__ void k_ctl_check(DevCtl* t, const DevScalars* sc, Handle h_full, int nk) {
+  t->kernels += nk;
+  t->grad_evals += 1;
+  t->grad_ffts += 1;
+  t->grad_ffts_fp64 += 1;
+  const double gnorm = sqrt(sc->red[2]), f = f_of(sc);
+  const bool pass = t->check && isfinite(gnorm) && isfinite(f) && t->g0 > 0.0 &&
+                    gnorm / t->g0 < t->tol;
+  cudaGraphSetConditional(h_full, pass ? 0u : 1u);
+}
+
+__global__ void k_ctl_full(DevCtl* t, int nk) {
+  t->kernels += nk;
   t->grad_evals += 1;
   t->grad_ffts += 1;
   t->grad_ffts_fp64 += 1;
@@ -398,7 +422,7 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   const Fields f32a{F[0], F[2], F[4], F[6], F[8]}, f32b{F[1], F[3], F[5], F[7], F[9]};
   const Fields f64a{s_out, F[2], F[4], F[6], F[8]}, f64b{F[1], F[3], F[5], F[7], F[9]};
 
-  Handle h_newton, h_switch, h_step, h_first;
+  Handle h_newton, h_switch, h_step, h_first, h_full;
   StepHandles hs;
   auto mk = [&](Handle* h) {
     check(cudaGraphConditionalHandleCreate(h, top, 0, cudaGraphCondAssignDefault), "handle");
@@ -410,6 +434,14 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   // a conditional node for the graph to instantiate)
   const int first = o.start != 1 ? 0 : (o.g0_norm > 0.0 ? 2 : 1);
   if (first == 1) mk(&h_first);
+  // the switch's sums-only check: mixed solves of lengths with float-float
+  // transforms (a four-step schedule)
+  bool has_check = false;
+  if constexpr (kMixed) {
+    for (const FourStepShape& q : kFourStep)
+      if (q.n == c->n && q.f1 == c->plan.f1 && q.f2 == c->plan.f2) has_check = true;
+  }
+  if (has_check) mk(&h_full);
   const int nvar = kMixed ? 4 : 2;
   for (int v = 0; v < nvar; ++v) {
     mk(&hs.cg[v]);
@@ -488,15 +520,37 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
           k_to_fp64<<<pointwise_blocks((long long)c->n3(), c->sms), kThreads, 0, c->stream>>>(
               t, s_out, as<float>(f32a.s), as<float>(f32b.s), c->n3());
           check(cudaGetLastError(), "k_to_fp64");
-          grad_newton<double, double, TC>(c, s_out, w, N, nbar, as<double>(f64a.y),
-                                          as<double>(f64a.g), as<TC>(f64a.D), as<TC>(f64a.r), jac);
-          const int nk1 = (int)(total_launches(c) - k1) + 2;
-          k_ctl_switched<<<1, 1, 0, c->stream>>>(t, nk1);
+          auto full = [&]() {
+            grad_newton<double, double, TC>(c, s_out, w, N, nbar, as<double>(f64a.y),
+                                            as<double>(f64a.g), as<TC>(f64a.D),
+                                            as<TC>(f64a.r), jac);
+          };
+          if (has_check) {
+            // the FP64 gradient's sums first; the full gradient in an IF node
+            grad_sums_ff(c, s_out, w, N, nbar, jac);
+            const int nk_check = (int)(total_launches(c) - k1) + 1;
+            k_ctl_check<<<1, 1, 0, c->stream>>>(t, c->sc, h_full, nk_check);
+            check(cudaGetLastError(), "k_ctl_check");
+            cudaGraph_t fbody;
+            add_conditional(c->stream, h_full, cudaGraphCondTypeIf, 1, &fbody);
+            capture_into(c, fbody, st[3], [&]() {
+              const long long k2 = total_launches(c);
+              full();
+              const int nk_full = (int)(total_launches(c) - k2) + 1;
+              k_ctl_full<<<1, 1, 0, c->stream>>>(t, nk_full);
+              check(cudaGetLastError(), "k_ctl_full");
+            });
+            k_ctl_switched<<<1, 1, 0, c->stream>>>(t, 2, 0);   // it and k_to_fp64
+          } else {
+            full();
+            const int nk1 = (int)(total_launches(c) - k1) + 2;
+            k_ctl_switched<<<1, 1, 0, c->stream>>>(t, nk1, 1);
+          }
           check(cudaGetLastError(), "k_ctl_switched");
         });
       } else {
         capture_into(c, sbody, st[2], [&]() {
-          k_ctl_switched<<<1, 1, 0, c->stream>>>(t, 1);   // never taken: FP64 throughout
+          k_ctl_switched<<<1, 1, 0, c->stream>>>(t, 1, 1);   // never taken: FP64 throughout
           check(cudaGetLastError(), "k_ctl_switched");
         });
       }

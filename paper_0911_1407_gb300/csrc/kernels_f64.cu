@@ -4,6 +4,10 @@
 #include "launch.cuh"
 
 namespace plc {
+bool grad_sums_ff(plc_ctx* c, const double* s, const double* w, const int32_t* N, double nbar,
+                  bool jac) {
+  return grad_sums_ff_impl(c, s, w, N, nbar, jac);
+}
 template void prior_apply<double>(plc_ctx*, const double*, double*);
 template void hessvec_s<double>(plc_ctx*, const double*, const double*, double, const double*, double*);
 template void grad_public<double>(plc_ctx*, const double*, const double*, const int32_t*, double,

@@ -175,14 +175,26 @@ void grad_newton(plc_ctx* c, const TS* s, const double* w, const int32_t* N, dou
   if constexpr (std::is_same<T, double>::value && std::is_same<TC, float>::value) {
     // the FP64 gradient of the mixed solve: float-float transforms and
     // epilogue where the length has a four-step schedule
-    const EpiGradFF epi{s, w, N, ff(nbar), ff(c->mu), y, g, D, r, (float)c->jac_c, jac ? 1 : 0,
-                        static_cast<const ff*>(c->expff)};
+    const EpiGradFF<true> epi{s, w, N, ff(nbar), ff(c->mu), y, g, D, r, (float)c->jac_c,
+                              jac ? 1 : 0, static_cast<const ff*>(c->expff)};
     if (run_four_step<ff>(c, ProShiftFF{s, ff(c->mu)}, epi, FinGrad{}, 0, nullptr, S_GXFF)) return;
   }
   run_pipeline<T>(c, ProShift<T, TS>{s, c->mu},
                   EpiGrad<T, TS, double, TC>{s, w, N, nbar, c->mu, y, g, D, r, c->jac_c,
                                              jac ? 1 : 0},
                   FinGrad{}, 0, nullptr, true);
+}
+
+// The sums of the FP64 gradient of the mixed solve at an FP64 s (the
+// float-float pipeline with nothing stored: -ln P, ||g||^2 and the scale of
+// the rounding test into sc->red, FinGrad), for a stopping test that may end
+// the solve before the gradient's fields are needed.  False (nothing run)
+// when the length has no four-step schedule.
+inline bool grad_sums_ff_impl(plc_ctx* c, const double* s, const double* w, const int32_t* N,
+                              double nbar, bool jac) {
+  const EpiGradFF<false> epi{s, w, N, ff(nbar), ff(c->mu), nullptr, nullptr, nullptr, nullptr,
+                             (float)c->jac_c, jac ? 1 : 0, static_cast<const ff*>(c->expff)};
+  return run_four_step<ff>(c, ProShiftFF{s, ff(c->mu)}, epi, FinGrad{}, 0, nullptr, S_GXFF);
 }
 
 template <typename T, typename TS, typename TC>

@@ -132,8 +132,9 @@ struct ProShiftFF {
 // gradient of the mixed solve), kept in float-float: y (from the transform),
 // s (FP64 in memory, split by its bit fields), D = nbar w e^s (exp_ff),
 // g = y + D - N and the six sums of EpiGrad are float-float; y and g are
-// stored in FP64, D and r = -g in FP32.
-struct EpiGradFF {
+// stored in FP64, D and r = -g in FP32.  With STORE false nothing is stored
+// (the sums alone, for a stopping test that may end the solve).
+template <bool STORE = true> struct EpiGradFF {
   static constexpr int NV = 6;
   static constexpr unsigned MAXMASK = 0;
   using Acc = AccFF;
@@ -176,15 +177,19 @@ struct EpiGradFF {
       acc[4].add(ni * ff_abs(st));
       const float gc = gi.hi + gi.lo, dc = d.hi + d.lo;
       acc[5].add(ff(jac ? gc * jacobi(gc, dc, c) : gc * gc, 0.f));
-      yo.v[j] = to_double(y.v[j]);
-      go.v[j] = to_double(gi);
-      dv.v[j] = dc;
-      rv.v[j] = -gc;
+      if constexpr (STORE) {
+        yo.v[j] = to_double(y.v[j]);
+        go.v[j] = to_double(gi);
+        dv.v[j] = dc;
+        rv.v[j] = -gc;
+      }
     }
-    if (yout) st4(yout + i, yo);
-    if (g) st4(g + i, go);
-    if (D) st4(D + i, dv);
-    if (r) st4(r + i, rv);
+    if constexpr (STORE) {
+      if (yout) st4(yout + i, yo);
+      if (g) st4(g + i, go);
+      if (D) st4(D + i, dv);
+      if (r) st4(r + i, rv);
+    }
   }
 };
 

@@ -408,7 +408,7 @@ template <typename Epi> struct EpiUnroll<Epi, decltype((void)Epi::kUnroll)> {
 template <typename Epi> struct XiMinBlocks {
   static constexpr int value = 1;
 };
-template <> struct XiMinBlocks<EpiGradFF> {
+template <bool STORE> struct XiMinBlocks<EpiGradFF<STORE>> {
   static constexpr int value = 3;
 };
 

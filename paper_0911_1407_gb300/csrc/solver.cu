@@ -109,6 +109,11 @@ struct Lognormal {
                        T* y, T* g, TC* D, TC* r, bool jac) {
     grad_newton<T, TS, TC>(c, s, w, N, nbar, y, g, D, r, jac);
   }
+  // the sums of the FP64 gradient alone (false: not offered for this length)
+  static bool gradient_sums(plc_ctx* c, const double* s, const double* w, const int32_t* N,
+                            double nbar, bool jac) {
+    return grad_sums_ff(c, s, w, N, nbar, jac);
+  }
   template <typename T, typename TC>
   static void trial(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
                     const TC* D, const int32_t* N, const double* w, double nbar, double tau,
@@ -131,6 +136,9 @@ struct GaussPrior {
   static void gradient(plc_ctx* c, const TS* s, const double* w, const int32_t* N, double nbar,
                        T* y, T* g, TC* D, TC* r, bool jac) {
     grad_newton_g<T, TS, TC>(c, s, w, N, nbar, y, g, D, r, jac);
+  }
+  static bool gradient_sums(plc_ctx*, const double*, const double*, const int32_t*, double, bool) {
+    return false;
   }
   template <typename T, typename TC>
   static void trial(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
@@ -157,6 +165,7 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
   State alt{F[1], F[3], F[5], F[7], F[9]};
 
   plc_stats S{};
+  double g0 = 0.0;   // ||g0|| of the stopping test (set below)
   // y, g, D, r and the sums at cur.s through the FFT (phase precision)
   auto fft_gradient = [&]() {
     if (fp64) {
@@ -191,12 +200,24 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
     S.grad_evals += 1;
     return grad_sums(c);
   };
-  // move the FP32 state to FP64: s in the caller's buffer, fresh FP64 gradient
-  auto to_fp64 = [&]() {
+  // move the FP32 state to FP64: s in the caller's buffer, fresh FP64
+  // gradient.  When the FP32 gradient already passes the stopping test
+  // (check), the FP64 gradient's sums are taken first without its fields:
+  // if they pass too the solve ends there, else the full gradient follows.
+  auto to_fp64 = [&](bool check) {
     if constexpr (kMixed) convert<double, float>(c, as<float>(cur.s), s_out);
     fp64 = true;
     cur.s = s_out;
     alt.s = F[1];
+    if (check && Model::gradient_sums(c, s_out, w, N, nbar, jac)) {
+      read_scalars(c);
+      S.grad_evals += 1;
+      S.grad_ffts += 1;
+      S.grad_ffts_fp64 += 1;
+      const GradSums gc = grad_sums(c);
+      const double rel = std::sqrt(gc.gg) / g0;
+      if (rel < o.tol && std::isfinite(gc.f())) return gc;
+    }
     return fft_gradient();
   };
 
@@ -205,7 +226,7 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
   // there serves only this norm: none is taken when g0_norm is given, and
   // at the prior mean it needs no transform.
   GradSums gs{};
-  double g0 = o.g0_norm;
+  g0 = o.g0_norm;
   bool first = true;
   if (o.start == 1) {
     if (g0 > 0.0) {
@@ -252,7 +273,7 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
     // halve the gradient (the FP32 rounding floor)
     if (!fp64 && (rel < o.mixed_switch || rel < o.tol ||
                   (it > 0 && rel < 1e-3 && rel > 0.5 * prev_rel))) {
-      gs = to_fp64();
+      gs = to_fp64(rel < o.tol);
       continue;
     }
     prev_rel = rel;
