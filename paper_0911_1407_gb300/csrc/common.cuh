@@ -428,10 +428,24 @@ __device__ __forceinline__ void grid_finish(double* v, const RedArgs& ra, Fin fi
   double acc[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) acc[j] = red_identity<MAXMASK>(j);
-  for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+  // U partials per thread loaded before they are summed (in the same
+  // order, b = tid, tid + blockDim, ...), so that the last block waits for
+  // about one L2 round trip per U instead of one per partial: this runs
+  // while the rest of the GPU waits for the kernel to end
+  constexpr int U = NV <= 1 ? 8 : (NV <= 3 ? 4 : 2);
+  for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * blockDim.x) {
+    double t[U][NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j)
-      acc[j] = red_op<MAXMASK>(j, acc[j], __ldcg(ra.partials + (size_t)b * kMaxRed + j));
+    for (int u = 0; u < U; ++u) {
+      const unsigned b = b0 + u * blockDim.x;
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        t[u][j] = b < nblocks ? __ldcg(ra.partials + (size_t)b * kMaxRed + j) : red_identity<MAXMASK>(j);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) acc[j] = red_op<MAXMASK>(j, acc[j], t[u][j]);
   }
   block_reduce<NV, MAXMASK>(acc, sh);
   if (threadIdx.x == 0) {
