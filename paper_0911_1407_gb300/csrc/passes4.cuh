@@ -304,6 +304,14 @@ template <typename Pro> struct XfMinBlocks {
 template <> struct XfMinBlocks<ProShiftFF> {
   static constexpr int value = 3;
 };
+// Prologue steps (four x each) a thread keeps in flight: eight, or
+// Pro::kBatch where the prologue sets one.
+template <typename Pro, typename = void> struct XfBatch {
+  static constexpr int value = 8;
+};
+template <typename Pro> struct XfBatch<Pro, decltype((void)Pro::kBatch)> {
+  static constexpr int value = Pro::kBatch;
+};
 
 template <typename T, int N1, int N2, typename Pro>
 __global__ void __launch_bounds__(kThreads, XfMinBlocks<Pro>::value)
@@ -313,10 +321,9 @@ k4_xf(Pro pro, cpx<T>* __restrict__ A, const cpx<T>* __restrict__ twg,
   pro.prepare();
   const int h = N / 2 + 1, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
   // prologue: 32 rows in natural order, four x per thread and step, up to
-  // eight steps' loads in flight per thread (measured 59.6 us against 62 with
-  // four at 256^3); the block's rows are contiguous and are first requested
-  // into L2 whole
-  constexpr int Q = N / 4, TOT = Gm::RY * Q, B4 = 8;
+  // XfBatch steps' loads in flight per thread; the block's rows are
+  // contiguous and are first requested into L2 whole
+  constexpr int Q = N / 4, TOT = Gm::RY * Q, B4 = XfBatch<Pro>::value;
   const size_t row0 = ((size_t)z * N + y0) * N;
   if (threadIdx.x == 0) pro.prefetch(row0, Gm::RY * N);
   for (int base = threadIdx.x; base < TOT; base += B4 * kThreads) {
