@@ -139,3 +139,22 @@ def test_batch_equals_one_by_one(plc):
     assert st2 == 0
     for r, s in zip(singles, ss):
         assert torch.equal(r.s, s)
+
+
+@pytest.mark.parametrize("tol", [4e-7, 3e-7, 2e-7, 1.5e-7, 1e-7])
+def test_drivers_agree_near_the_fp32_floor(plc, tol):
+    """Mixed solves whose tolerance sits near the FP32 gradient's rounding
+    floor: at the switch the FP64 gradient's sums are taken first when the
+    FP32 gradient passes the test, and the full FP64 gradient (and more
+    Newton steps) follows when the FP64 sums fail it.  Whichever branch a
+    tolerance takes, both drivers take it identically and the solve meets
+    its tolerance on the FP64 gradient."""
+    m = mocks.make_mock(mocks.WORKLOADS["plain32"])
+    c = _ctx(plc, m, "mixed")
+    rh = _solve(c, m, 0, tol=tol)
+    rd = _solve(c, m, 1, tol=tol)
+    assert rh.status == 0 and rd.status == 0
+    for k in ITER_KEYS:
+        assert rh.stats[k] == rd.stats[k], k
+    assert torch.equal(rh.s, rd.s)
+    assert rd.stats["grad_rel"] < tol and rd.stats["grad_ffts_fp64"] >= 1
