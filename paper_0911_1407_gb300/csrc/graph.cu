@@ -161,6 +161,14 @@ __global__ void k_ctl_check(DevCtl* t, const DevScalars* sc, Handle h_full, int 
   cudaGraphSetConditional(h_full, pass ? 0u : 1u);
 }
 
+// Before the switch's check: run it only when the FP32 gradient passed the
+// stopping test; the full FP64 gradient follows otherwise (k_ctl_check
+// decides when the check runs).
+__global__ void k_ctl_presw(const DevCtl* t, Handle h_chk, Handle h_full) {
+  cudaGraphSetConditional(h_chk, t->check ? 1u : 0u);
+  cudaGraphSetConditional(h_full, t->check ? 0u : 1u);
+}
+
 __global__ void k_ctl_full(DevCtl* t, int nk) {
   t->kernels += nk;
   t->grad_evals += 1;
@@ -422,7 +430,7 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   const Fields f32a{F[0], F[2], F[4], F[6], F[8]}, f32b{F[1], F[3], F[5], F[7], F[9]};
   const Fields f64a{s_out, F[2], F[4], F[6], F[8]}, f64b{F[1], F[3], F[5], F[7], F[9]};
 
-  Handle h_newton, h_switch, h_step, h_first, h_full;
+  Handle h_newton, h_switch, h_step, h_first, h_full, h_chk;
   StepHandles hs;
   auto mk = [&](Handle* h) {
     check(cudaGraphConditionalHandleCreate(h, top, 0, cudaGraphCondAssignDefault), "handle");
@@ -441,7 +449,10 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
     for (const FourStepShape& q : kFourStep)
       if (q.n == c->n && q.f1 == c->plan.f1 && q.f2 == c->plan.f2) has_check = true;
   }
-  if (has_check) mk(&h_full);
+  if (has_check) {
+    mk(&h_full);
+    mk(&h_chk);
+  }
   const int nvar = kMixed ? 4 : 2;
   for (int v = 0; v < nvar; ++v) {
     mk(&hs.cg[v]);
@@ -526,12 +537,20 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
                                             as<TC>(f64a.r), jac);
           };
           if (has_check) {
-            // the FP64 gradient's sums first; the full gradient in an IF node
-            grad_sums_ff(c, s_out, w, N, nbar, jac);
-            const int nk_check = (int)(total_launches(c) - k1) + 1;
-            k_ctl_check<<<1, 1, 0, c->stream>>>(t, c->sc, h_full, nk_check);
-            check(cudaGetLastError(), "k_ctl_check");
-            cudaGraph_t fbody;
+            // when the FP32 gradient passed the stopping test, the FP64
+            // gradient's sums first (an IF node); the full gradient in a
+            // second IF node, unless those sums pass it too
+            k_ctl_presw<<<1, 1, 0, c->stream>>>(t, h_chk, h_full);
+            check(cudaGetLastError(), "k_ctl_presw");
+            cudaGraph_t cbody, fbody;
+            add_conditional(c->stream, h_chk, cudaGraphCondTypeIf, 1, &cbody);
+            capture_into(c, cbody, st[3], [&]() {
+              const long long k2 = total_launches(c);
+              grad_sums_ff(c, s_out, w, N, nbar, jac);
+              const int nk_check = (int)(total_launches(c) - k2) + 1;
+              k_ctl_check<<<1, 1, 0, c->stream>>>(t, c->sc, h_full, nk_check);
+              check(cudaGetLastError(), "k_ctl_check");
+            });
             add_conditional(c->stream, h_full, cudaGraphCondTypeIf, 1, &fbody);
             capture_into(c, fbody, st[3], [&]() {
               const long long k2 = total_launches(c);
@@ -540,7 +559,8 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
               k_ctl_full<<<1, 1, 0, c->stream>>>(t, nk_full);
               check(cudaGetLastError(), "k_ctl_full");
             });
-            k_ctl_switched<<<1, 1, 0, c->stream>>>(t, 2, 0);   // it and k_to_fp64
+            // it, k_to_fp64 and k_ctl_presw
+            k_ctl_switched<<<1, 1, 0, c->stream>>>(t, 3, 0);
           } else {
             full();
             const int nk1 = (int)(total_launches(c) - k1) + 2;
