@@ -332,10 +332,10 @@ def cpu_full(args):
         print(json.dumps({key: out}), flush=True)
     rec["bias64"] = bias64_vs_oracle(plc, err)
     print(json.dumps({"bias64": rec["bias64"]}), flush=True)
-    out = args.out or os.path.join(ROOT, "gpurun_out", "cpu_full.json")
-    os.makedirs(os.path.dirname(out), exist_ok=True)
-    with open(out, "w") as f:
-        json.dump(rec, f, indent=1)
+    if args.out:
+        os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+        with open(args.out, "w") as f:
+            json.dump(rec, f, indent=1)
     print(json.dumps(rec), flush=True)
     return 0
 
