@@ -96,39 +96,51 @@ __device__ __forceinline__ void phase_b_inv(cpx<T>* v, const cpx<T>* tw2, int k1
   }
 }
 
-#define PLC_PASS4_PROLOGUE(SMEM_TAIL)                                   \
+#define PLC_PASS4_SETUP(SMEM_TAIL)                                      \
   using Gm = Geo4<T, N1, N2>;                                           \
   using C = cpx<T>;                                                     \
   constexpr int N = Gm::N;                                              \
   if (done && *done) return;                                            \
   extern __shared__ __align__(16) unsigned char smem_raw[];             \
   C* tw2 = reinterpret_cast<C*>(smem_raw);                              \
-  SMEM_TAIL;                                                            \
+  SMEM_TAIL
+
+#define PLC_PASS4_PROLOGUE(SMEM_TAIL)                                   \
+  PLC_PASS4_SETUP(SMEM_TAIL);                                           \
   load_tw2<C, N1, N2>(tw2, twg);                                        \
   __syncthreads()
 
 // ---------------------------------------------------------------------------
 // YF: c2c along y.  grid = (n / 16, n/2+1); block (zb, kx) owns the lines
-// A[z0 + c][kx][:] and writes B[kx][:][z0 + c].
+// A[z0 + c][kx][:] and writes B[kx][:][z0 + c].  As in the z and y-inverse
+// passes, a phase whose tasks match the threads one to one is compiled
+// without its guard or task loop.
 // ---------------------------------------------------------------------------
 template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(kThreads)
 k4_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, const cpx<T>* __restrict__ twg,
       const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(C* X = tw2 + N);
+  PLC_PASS4_SETUP(C* X = tw2 + N);
   const int h = N / 2 + 1, z0 = blockIdx.x * Gm::L, kx = blockIdx.y;
-  if (threadIdx.x < Gm::L * N2) {
-    const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
+  const bool task_a = Gm::L * N2 == kThreads || threadIdx.x < Gm::L * N2;
+  const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
+  // the lines are loaded before the twiddle table, so that the two loads
+  // overlap instead of waiting one after the other at its barrier
+  C v[N1];
+  if (task_a) {
     const C* src = A + ((size_t)(z0 + c) * h + kx) * N + n2;
-    C v[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[N2 * n1];
+  }
+  load_tw2<C, N1, N2>(tw2, twg);
+  __syncthreads();
+  if (task_a) {
     phase_a<T, N1, N2, -1>(v, tw2, n2);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) X[c * Gm::S + k1 * N2 + n2] = v[k1];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
+  auto task_b = [&](int t) {
     const int c = t % Gm::L, k1 = t / Gm::L;
     C v[N2];
 #pragma unroll
@@ -137,6 +149,11 @@ k4_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, const cpx<T>* __rest
     C* dst = B + ((size_t)kx * N + k1) * N + z0 + c;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) dst[(size_t)N1 * k2 * N] = v[k2];
+  };
+  if constexpr (Gm::L * N1 == kThreads) {
+    task_b(threadIdx.x);
+  } else {
+    for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) task_b(t);
   }
 }
 
@@ -145,20 +162,36 @@ k4_yf(const cpx<T>* __restrict__ A, cpx<T>* __restrict__ B, const cpx<T>* __rest
 __device__ __forceinline__ float as_mult(float m, float) { return m; }
 __device__ __forceinline__ ff as_mult(double m, ff) { return ff_split(m); }
 
+// Resident blocks per SM asked of the compiler for the z pass.  FP32 at
+// 16 x 16: three blocks (up to 85 registers, it takes 69) ran the pass at
+// 256^3 in 32.8 us against 36.9 us at four blocks of 59 registers on
+// L2-resident data, and in 36.8 against 38.9 us inside the solve, with
+// identical results; the more registers let it keep more loads in flight.
+// Elsewhere 0, which leaves the register budget to the compiler as a bound
+// without a block count does (a count of 1 changes it).
+template <typename T, int N1, int N2> struct ZMinBlocks { static constexpr int value = 0; };
+template <> struct ZMinBlocks<float, 16, 16> { static constexpr int value = 3; };
+
 // ---------------------------------------------------------------------------
 // Z: forward c2c along z, times M[|m|^2] = 1/(lambda_k n^3), inverse c2c,
 // in place.  grid = (n / 16, n/2+1); block (kyb, kx) owns B[kx][ky0 + c][:].
 // The spectrum of each phase-B task stays in registers between the two
-// transforms.  zero_dc drops the DC mode.
+// transforms.  zero_dc drops the DC mode.  Where every thread holds exactly
+// one task of each phase (L N1 = L N2 = kThreads) the guards and the task
+// loop are compiled out.
 // ---------------------------------------------------------------------------
 template <typename T, int N1, int N2, typename TM>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, ZMinBlocks<T, N1, N2>::value)
 k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
      const cpx<T>* __restrict__ twg, const int* __restrict__ done) {
   PLC_PASS4_PROLOGUE(C* X = tw2 + N; T* Ms = reinterpret_cast<T*>(X + Gm::L * Gm::S));
-  const int ky0 = blockIdx.x * Gm::L, kx = blockIdx.y;
+  // planes in decreasing kx: the y-forward pass before it writes them in
+  // increasing kx, so the most recently written (most likely still in L2)
+  // are read first
+  const int ky0 = blockIdx.x * Gm::L, kx = N / 2 - blockIdx.y;
   C* line0 = B + ((size_t)kx * N + ky0) * N;
-  const bool task_a = threadIdx.x < Gm::L * N2;
+  constexpr bool kOneA = Gm::L * N2 == kThreads, kOneB = Gm::L * N1 == kThreads;
+  const bool task_a = kOneA || threadIdx.x < Gm::L * N2;
   const int n2a = threadIdx.x % N2, ca = threadIdx.x / N2;
   C v[N1 > N2 ? N1 : N2];
   if (task_a) {
@@ -190,7 +223,7 @@ k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
     for (int k1 = 0; k1 < N1; ++k1) X[ca * Gm::S + k1 * N2 + n2a] = v[k1];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
+  auto task_b = [&](int t) {
     const int c = t % Gm::L, k1 = t / Gm::L;
     C u[N2];
 #pragma unroll
@@ -204,6 +237,11 @@ k4_z(cpx<T>* __restrict__ B, const TM* __restrict__ M, int zero_dc,
     phase_b_inv<T, N1, N2>(u, tw2, k1);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = u[n2];
+  };
+  if constexpr (kOneB) {
+    task_b(threadIdx.x);
+  } else {
+    for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) task_b(t);
   }
   __syncthreads();
   if (task_a) {
@@ -226,7 +264,7 @@ k4_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, const cpx<T>* __rest
       const int* __restrict__ done) {
   PLC_PASS4_PROLOGUE(C* X = tw2 + N);
   const int h = N / 2 + 1, z0 = blockIdx.x * Gm::L, kx = blockIdx.y;
-  for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) {
+  auto task_b = [&](int t) {
     const int c = t % Gm::L, k1 = t / Gm::L;
     const C* src = B + ((size_t)kx * N + k1) * N + z0 + c;
     C u[N2];
@@ -235,9 +273,14 @@ k4_yi(const cpx<T>* __restrict__ B, cpx<T>* __restrict__ A, const cpx<T>* __rest
     phase_b_inv<T, N1, N2>(u, tw2, k1);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) X[c * Gm::S + k1 * N2 + n2] = u[n2];
+  };
+  if constexpr (Gm::L * N1 == kThreads) {
+    task_b(threadIdx.x);
+  } else {
+    for (int t = threadIdx.x; t < Gm::L * N1; t += kThreads) task_b(t);
   }
   __syncthreads();
-  if (threadIdx.x < Gm::L * N2) {
+  if (Gm::L * N2 == kThreads || threadIdx.x < Gm::L * N2) {
     const int n2 = threadIdx.x % N2, c = threadIdx.x / N2;
     C v[N1];
 #pragma unroll
@@ -317,7 +360,11 @@ template <typename T, int N1, int N2, typename Pro>
 __global__ void __launch_bounds__(kThreads, XfMinBlocks<Pro>::value)
 k4_xf(Pro pro, cpx<T>* __restrict__ A, const cpx<T>* __restrict__ twg,
       const int* __restrict__ done) {
-  PLC_PASS4_PROLOGUE(T* R = reinterpret_cast<T*>(tw2 + N); C* X = tw2 + N);
+  PLC_PASS4_SETUP(T* R = reinterpret_cast<T*>(tw2 + N); C* X = tw2 + N);
+  // the twiddle table is first read after the barrier that ends the
+  // prologue, which publishes it with the rows: it needs no barrier of its
+  // own, and the row loads do not wait for it
+  load_tw2<C, N1, N2>(tw2, twg);
   pro.prepare();
   const int h = N / 2 + 1, z = blockIdx.y, y0 = blockIdx.x * Gm::RY;
   // prologue: 32 rows in natural order, four x per thread and step, up to
@@ -497,5 +544,6 @@ k4_xi(const cpx<T>* __restrict__ A, Epi epi, Fin fin, RedArgs ra,
 }
 
 #undef PLC_PASS4_PROLOGUE
+#undef PLC_PASS4_SETUP
 
 }  // namespace plc
