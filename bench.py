@@ -126,19 +126,21 @@ def algorithmic_bytes(n: int) -> dict:
         "yf_f32": 2 * spec32, "z_f32": 2 * spec32, "yi_f32": 2 * spec32,
         "xi_f32": spec32 + 3 * 4 * n3,          # read spectrum, D, p; write Hp
         # FFT gradients (w = 1): read s, write the spectrum; read the
-        # spectrum, s, N, write y, g, D, r (FP32 phase: all FP32; FP64
-        # context: y, g, D, r in FP64)
+        # spectrum, s, N, write y, D, r (FP32 phase: all FP32, no g, which
+        # the trial forms again from y, D and N) or y, g, D, r (FP64 context,
+        # y and g in FP64)
         "grad_xf_f32": 4 * n3 + spec32,
         "grad_yf_f32": 2 * spec32, "grad_z_f32": 2 * spec32, "grad_yi_f32": 2 * spec32,
-        "grad_xi_f32": spec32 + (4 + 4 + 4 * 4) * n3,
+        "grad_xi_f32": spec32 + (4 + 4 + 3 * 4) * n3,
         "grad_xf_f64": 8 * n3 + spec64,
         "grad_yf_f64": 2 * spec64, "grad_z_f64": 2 * spec64, "grad_yi_f64": 2 * spec64,
         "grad_xi_f64": spec64 + (8 + 4 + 4 * 8) * n3,
         # read x, p, r, Hp, D; write x, r (the first iteration of a solve
         # writes x = alpha p without reading x: 4 bytes less, see main)
         "cg_update_f32": 7 * 4 * n3,
-        # line-search trial: read xi, r, D, s, y, g, N; write s, y, g, D, r
-        "newton_update_f32": (7 * 4 + 5 * 4) * n3,
+        # line-search trial: read xi, r, D, s, y, N; write s, y, D, r (the
+        # FP32 phase keeps no g); FP64 phase: also read and write g
+        "newton_update_f32": (6 * 4 + 4 * 4) * n3,
         "newton_update_f64": (3 * 4 + 3 * 8 + 4 + 3 * 8 + 2 * 4) * n3,
     }
 

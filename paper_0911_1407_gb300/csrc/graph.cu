@@ -362,9 +362,12 @@ void capture_step(plc_ctx* c, const std::vector<cudaStream_t>& st, int lv, DevCt
   add_conditional(st[lv], h_ls, cudaGraphCondTypeWhile, 1, &body);
   capture_into(c, body, st[lv + 1], [&]() {
     const long long k0 = total_launches(c);
-    newton_update<T, TC>(c, as<T>(cur.s), as<T>(cur.y), as<T>(cur.g), as<TC>(cur.r), x,
-                         as<TC>(cur.D), N, w, nbar, 0.0, jac, as<T>(alt.s), as<T>(alt.y),
-                         as<T>(alt.g), as<TC>(alt.D), as<TC>(alt.r), &c->sc->tau);
+    // the FP32 phase keeps no g: the trial forms it again from y, D and N
+    constexpr bool kNoG = std::is_same<T, float>::value;
+    newton_update<T, TC>(c, as<T>(cur.s), as<T>(cur.y), kNoG ? nullptr : as<T>(cur.g),
+                         as<TC>(cur.r), x, as<TC>(cur.D), N, w, nbar, 0.0, jac, as<T>(alt.s),
+                         as<T>(alt.y), kNoG ? nullptr : as<T>(alt.g), as<TC>(alt.D),
+                         as<TC>(alt.r), &c->sc->tau);
     const int nk = (int)(total_launches(c) - k0) + 1;
     k_ctl_ls<<<1, 1, 0, c->stream>>>(t, c->sc, h_ls, nk);
     check(cudaGetLastError(), "k_ctl_ls");
@@ -473,7 +476,7 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
       } else if constexpr (kMixed) {
         convert<float, double>(c, s_out, as<float>(f32a.s));
         grad_newton<float, float, float>(c, as<float>(f32a.s), w, N, nbar, as<float>(f32a.y),
-                                         as<float>(f32a.g), as<float>(f32a.D),
+                                         nullptr, as<float>(f32a.D),
                                          as<float>(f32a.r), jac);
       }
     };
@@ -510,7 +513,7 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
       } else if constexpr (kMixed) {
         diag_start<float>(c, as<float>(f32a.s), N, w, nbar);
         grad_newton<float, float, float>(c, as<float>(f32a.s), w, N, nbar, as<float>(f32a.y),
-                                         as<float>(f32a.g), as<float>(f32a.D), as<float>(f32a.r),
+                                         nullptr, as<float>(f32a.D), as<float>(f32a.r),
                                          jac);
       }
       const int nk1 = (int)(total_launches(c) - k1) + 1;

@@ -285,6 +285,8 @@ template <typename T, typename TC>
 void newton_update(plc_ctx* c, const T* s, const T* y, const T* g, const TC* r, const TC* xi,
                    const TC* D, const int32_t* N, const double* w, double nbar, double tau,
                    bool jac, T* s2, T* y2, T* g2, TC* D2, TC* r2, const double* tau_dev) {
+  // g may be left out only where forming it again from y, D and N is exact
+  if (!g && !std::is_same<T, TC>::value) check(cudaErrorInvalidValue, "newton_update without g");
   LaunchScope ls(c, sizeof(T) == 4 ? S_NEWTON_UPDATE32 : S_NEWTON_UPDATE64);
   k_newton_update<T, TC><<<pw_blocks(c), kThreads, 0, c->stream>>>(
       s, y, g, r, xi, D, N, w, nbar, c->mu, tau, tau_dev, c->jac_c, jac ? 1 : 0, s2, y2, g2, D2, r2,

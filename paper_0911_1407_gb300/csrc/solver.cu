@@ -95,6 +95,8 @@ struct State {
 // boundary, tau <= 0.99 / max(-xi / (1 + delta)).
 struct Lognormal {
   static constexpr bool kBoundary = false;
+  // FP32 phase: g is not stored; the trial forms it from y, D and N
+  static constexpr bool kNoG32 = true;
   // ||g||^2 at the prior mean mu, where S^-1 (s - mu) = 0: g = nbar w e^mu - N
   static void g0_at_mean(plc_ctx* c, const double* s, const int32_t* N, const double* w,
                          double nbar) {
@@ -123,6 +125,7 @@ struct Lognormal {
 };
 struct GaussPrior {
   static constexpr bool kBoundary = true;
+  static constexpr bool kNoG32 = false;
   // ||g||^2 at delta = 0, the prior mean: g = nbar w - N
   static void g0_at_mean(plc_ctx* c, const double* s, const int32_t* N, const double* w,
                          double nbar) {
@@ -166,6 +169,7 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
 
   plc_stats S{};
   double g0 = 0.0;   // ||g0|| of the stopping test (set below)
+  auto g32 = [](const State& f) { return Model::kNoG32 ? nullptr : as<float>(f.g); };
   // y, g, D, r and the sums at cur.s through the FFT (phase precision)
   auto fft_gradient = [&]() {
     if (fp64) {
@@ -175,7 +179,7 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
       S.grad_ffts_fp64 += 1;
     } else if constexpr (kMixed) {
       Model::template gradient<float, float, float>(c, as<float>(cur.s), w, N, nbar,
-                                                    as<float>(cur.y), as<float>(cur.g),
+                                                    as<float>(cur.y), g32(cur),
                                                     as<float>(cur.D), as<float>(cur.r), jac);
     }
     read_scalars(c);
@@ -190,11 +194,10 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
                                         nbar, tau, jac, as<double>(alt.s), as<double>(alt.y),
                                         as<double>(alt.g), as<TC>(alt.D), as<TC>(alt.r));
     } else if constexpr (kMixed) {
-      Model::template trial<float, float>(c, as<float>(cur.s), as<float>(cur.y),
-                                          as<float>(cur.g), as<float>(cur.r), x,
-                                          as<float>(cur.D), N, w, nbar, tau, jac,
-                                          as<float>(alt.s), as<float>(alt.y), as<float>(alt.g),
-                                          as<float>(alt.D), as<float>(alt.r));
+      Model::template trial<float, float>(c, as<float>(cur.s), as<float>(cur.y), g32(cur),
+                                          as<float>(cur.r), x, as<float>(cur.D), N, w, nbar,
+                                          tau, jac, as<float>(alt.s), as<float>(alt.y),
+                                          g32(alt), as<float>(alt.D), as<float>(alt.r));
     }
     read_scalars(c);
     S.grad_evals += 1;
