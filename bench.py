@@ -537,9 +537,11 @@ def main(argv=None):
 
     driven = 0 if args.host_driven else 1
 
+    # each solve starts at mu (start=2: the start is the prior mean without
+    # an array holding it, so s is output only and needs no fill)
     def step():
-        s.fill_(m.mu)
-        return ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, device_driven=driven)
+        return ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, start=2,
+                                     device_driven=driven)
 
     # clocks are sampled from the warm-up on (nvidia-smi takes a moment to
     # start), through the end of the timed region: all under load
@@ -581,8 +583,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        s.fill_(m.mu)
-        ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, cg_chunk=1, device_driven=0)
+        ctx.newton_krylov_map(N_dev, None, m.nbar, s=s, tol=TOL, start=2, cg_chunk=1,
+                              device_driven=0)
     e1.record(stream)
     torch.cuda.synchronize()
     t_prof = e0.elapsed_time(e1) / 1e3
@@ -618,8 +620,7 @@ def main(argv=None):
             stream.wait_event(ev_in[b])
             if k >= 2:
                 stream.wait_event(ev_out[b])      # step k-2's MAP has left s_buf[b]
-            s_buf[b].fill_(m.mu)
-            ctx.newton_krylov_map(N_buf[b], None, m.nbar, s=s_buf[b], tol=TOL,
+            ctx.newton_krylov_map(N_buf[b], None, m.nbar, s=s_buf[b], tol=TOL, start=2,
                                   device_driven=driven)
             ev_solved[b].record(stream)
             with torch.cuda.stream(copy):

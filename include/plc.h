@@ -127,7 +127,13 @@ typedef struct {
                           Eq. MAPLNUB, resp. the domain root of the quadratic of
                           Eq. MAPG, cell by cell), 0 from the caller's start
                           itself.  ||g0|| of the stopping test is taken at the
-                          caller's start either way.  plc_bias_map ignores it. */
+                          caller's start either way.  2: as 1 with the caller's
+                          start taken to be the prior mean (mu, resp.
+                          delta = 0) without reading it: s_inout / delta_inout
+                          is output only, its contents on entry are ignored
+                          (the same iterates and result as 1 with the array
+                          filled with the mean, one field read and the fill
+                          saved).  plc_bias_map ignores it. */
 } plc_opts;
 
 typedef struct {
@@ -153,7 +159,8 @@ plc_status plc_default_opts(plc_opts* opts);
  * Armijo backtracking line search.  The prior term S^-1 (s - mu) is taken
  * through the FFT at the start (and, for PLC_MIXED, once when the state moves
  * from FP32 to FP64) and otherwise carried forward with S^-1 xi from the CG.  s_inout (double, device) holds the start
- * point on entry (e.g. filled with mu) and the MAP on exit.  N: int32 field;
+ * point on entry (e.g. filled with mu; not read with opts->start = 2) and
+ * the MAP on exit.  N: int32 field;
  * w: double field or NULL (double in both precisions).  opts NULL = defaults;
  * stats may be NULL.  Returns PLC_ERR_NOT_CONVERGED with s_inout holding the
  * last iterate when max_newton is reached.  Synchronises the stream. */

@@ -255,11 +255,17 @@ class Context:
 
     def newton_krylov_map(self, N, w, nbar: float, s: Optional[torch.Tensor] = None,
                           raise_on_fail: bool = True, **opts) -> MapResult:
-        """MAP; s (float64) is the start point and is overwritten (default mu)."""
+        """MAP; s (float64) is the start point and is overwritten (default mu).
+        With start=2, or with s omitted and start 1 (the default) or 2, the
+        start is mu without an array holding it: s is output only."""
         if s is None:
             if self.mu is None:
                 raise RuntimeError("set_prior first")
-            s = torch.full((self.n,) * 3, self.mu, dtype=torch.float64, device="cuda")
+            if opts.get("start", 1) >= 1:
+                s = torch.empty((self.n,) * 3, dtype=torch.float64, device="cuda")
+                opts["start"] = 2
+            else:
+                s = torch.full((self.n,) * 3, self.mu, dtype=torch.float64, device="cuda")
         o, stt = default_opts(**opts), Stats()
         st = self.lib.plc_newton_krylov_map(
             self._h, _ptr(N, self.n, torch.int32, "N"), _ptr(w, self.n, torch.float64, "w", False),
@@ -271,9 +277,15 @@ class Context:
     def gauss_map(self, N, w, nbar: float, delta: Optional[torch.Tensor] = None,
                   raise_on_fail: bool = True, **opts) -> MapResult:
         """MAP of the Gaussian-prior Poisson model; delta (float64) is the
-        start point (default 0) and is overwritten."""
+        start point (default 0) and is overwritten.  With start=2, or with
+        delta omitted and start 1 (the default) or 2, the start is 0 without
+        an array holding it: delta is output only."""
         if delta is None:
-            delta = torch.zeros((self.n,) * 3, dtype=torch.float64, device="cuda")
+            if opts.get("start", 1) >= 1:
+                delta = torch.empty((self.n,) * 3, dtype=torch.float64, device="cuda")
+                opts["start"] = 2
+            else:
+                delta = torch.zeros((self.n,) * 3, dtype=torch.float64, device="cuda")
         o, stt = default_opts(**opts), Stats()
         st = self.lib.plc_gauss_map(
             self._h, _ptr(N, self.n, torch.int32, "N"), _ptr(w, self.n, torch.float64, "w", False),

@@ -156,7 +156,7 @@ plc_status check_opts(plc_ctx* c, const plc_opts& o) {
   if (!(o.mixed_switch >= 0.0)) return fail(c, PLC_ERR_INVALID_ARG, "opts.mixed_switch must be >= 0");
   if (o.device_driven != 0 && o.device_driven != 1)
     return fail(c, PLC_ERR_INVALID_ARG, "opts.device_driven must be 0 or 1");
-  if (o.start != 0 && o.start != 1) return fail(c, PLC_ERR_INVALID_ARG, "opts.start must be 0 or 1");
+  if (o.start < 0 || o.start > 2) return fail(c, PLC_ERR_INVALID_ARG, "opts.start must be 0, 1 or 2");
   return PLC_OK;
 }
 

@@ -73,8 +73,9 @@ __device__ __forceinline__ double scale_of(const DevScalars* sc) {
 }
 
 // first: 0 the gradient at the caller's start ran, 1 it ran when the start
-// was off the prior mean (off_mean), 2 it did not run; nk_first: its kernels
-// when it ran conditionally.  g0 comes from red[2]: that gradient's, or the
+// was off the prior mean (off_mean), 2 it did not run (g0 given), 3 it did
+// not run (the start is the prior mean by definition); nk_first: its
+// kernels when it ran conditionally.  g0 comes from red[2]: that gradient's, or the
 // transform-free one at the prior mean.
 __global__ void k_ctl_init(DevCtl* t, const DevScalars* sc, CtlOpts o, Handle h_newton, int nk,
                            int first, int nk_first) {
@@ -443,7 +444,7 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
   mk(&h_step);
   // the first gradient's IF node, when there is one (a handle must belong to
   // a conditional node for the graph to instantiate)
-  const int first = o.start != 1 ? 0 : (o.g0_norm > 0.0 ? 2 : 1);
+  const int first = o.start == 0 ? 0 : (o.g0_norm > 0.0 ? 2 : (o.start == 2 ? 3 : 1));
   if (first == 1) mk(&h_first);
   // the switch's sums-only check: mixed solves of lengths with float-float
   // transforms (a four-step schedule)
@@ -497,13 +498,15 @@ void capture_solve(plc_ctx* c, cudaGraph_t top, const std::vector<cudaStream_t>&
         first_gradient();
         nk_first = (int)(total_launches(c) - k1);
       });
+    } else if (first == 3) {
+      g0_at_mean(c, nullptr, N, w, c->mu, nbar * std::exp(c->mu));
     } else if (first == 0) {
       first_gradient();
     }
     const int nk = (int)(total_launches(c) - k0) - nk_first + nk_ctl;
     k_ctl_init<<<1, 1, 0, c->stream>>>(t, c->sc, co, h_newton, nk, first, nk_first);
     check(cudaGetLastError(), "k_ctl_init");
-    if (o.start == 1) {
+    if (o.start >= 1) {
       // iterate from the per-cell diagonal-prior MAP (g0 stays at s_in)
       const long long k1 = total_launches(c);
       if (start64) {
@@ -646,7 +649,7 @@ plc_status newton_map_graph(plc_ctx* c, const int32_t* N, const double* w, doubl
   const void* kp[3] = {N, w, s_out};
   const double kv[9] = {nbar, o.tol, o.g0_norm, o.step_cap, o.eta_max, o.mixed_switch, c->mu,
                         c->jac_c, c->prior_var};
-  const int ki[4] = {o.max_newton, o.max_cg, o.precond * 2 + o.start,
+  const int ki[4] = {o.max_newton, o.max_cg, o.precond * 3 + o.start,
                      c->plan.f1 * 64 + c->plan.f2};
   SolveExec* e = nullptr;
   for (SolveExec& x : gs->cache)

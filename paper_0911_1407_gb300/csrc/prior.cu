@@ -171,7 +171,8 @@ void build_prior(plc_ctx* c, const double* lk_host, const double* lP_host, int n
 // factor nbar e^mu; Gaussian-prior model: mean 0, factor nbar).  Also sets
 // off_mean when s differs from the mean anywhere (compared bit for bit, so
 // -0.0 against +0.0 counts as different: the caller then takes the
-// transform).  ||g0|| only normalises the stop test: the Kahan FP32 sum
+// transform); s null: the start is the mean by definition, nothing is read
+// and off_mean is 0.  ||g0|| only normalises the stop test: the Kahan FP32 sum
 // (relative error ~1e-7) is ample.
 __global__ void __launch_bounds__(kThreads)
 k_g0_at_mean(const double* __restrict__ s, const int32_t* __restrict__ N,
@@ -189,10 +190,12 @@ k_g0_at_mean(const double* __restrict__ s, const int32_t* __restrict__ N,
 #pragma unroll
       for (int j = 0; j < 4; ++j) wv.v[j] = (float)wd.v[j];
     }
-    const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(s + i));
-    const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(s + i) + 1);
-    const bool off = a.x != mean_bits || a.y != mean_bits || b.x != mean_bits || b.y != mean_bits;
-    acc[1].max(off ? 1.f : 0.f);
+    if (s) {
+      const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(s + i));
+      const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(s + i) + 1);
+      const bool off = a.x != mean_bits || a.y != mean_bits || b.x != mean_bits || b.y != mean_bits;
+      acc[1].max(off ? 1.f : 0.f);
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float d = factor * wv.v[j] - (float)nv.v[j];

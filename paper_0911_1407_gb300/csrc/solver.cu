@@ -231,11 +231,13 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
   GradSums gs{};
   g0 = o.g0_norm;
   bool first = true;
-  if (o.start == 1) {
+  if (o.start >= 1) {
     if (g0 > 0.0) {
       first = false;
     } else {
-      Model::g0_at_mean(c, s_out, N, w, nbar);
+      // start 2: the caller's start is the prior mean by definition (s_out
+      // is not read)
+      Model::g0_at_mean(c, o.start == 2 ? nullptr : s_out, N, w, nbar);
       read_scalars(c);
       if (!c->sc_host->off_mean) {
         g0 = std::sqrt(c->sc_host->red[2]);
@@ -251,7 +253,7 @@ plc_status newton_map_model(plc_ctx* c, const int32_t* N, const double* w, doubl
     if (!(g0 > 0.0)) g0 = std::sqrt(gs.gg);
   }
   S.g0_norm = g0;
-  if (o.start == 1) {
+  if (o.start >= 1) {
     // iterate from the per-cell diagonal-prior MAP (g0 stays at s_in)
     if (fp64) Model::template start<double>(c, as<double>(cur.s), N, w, nbar);
     else if constexpr (kMixed) Model::template start<float>(c, as<float>(cur.s), N, w, nbar);

@@ -2,8 +2,9 @@
 
 Every case is made on the host; none can fault a GPU.
 
-* nbar <= 0, NaN or Inf: PLC_ERR_INVALID_ARG before any launch (the
-  context's launch counters stay at zero).
+* nbar <= 0, NaN or Inf, or opts.start outside {0, 1, 2}:
+  PLC_ERR_INVALID_ARG before any launch (the context's launch counters stay
+  at zero).
 * NaN or Inf in the selection w, or in the caller's start s0: the solve ends
   with PLC_ERR_NONFINITE, with no Newton step taken and finite statistics,
   in both drivers and both precisions.  A non-finite start reaches the
@@ -44,6 +45,19 @@ def test_bad_nbar_is_refused_before_any_launch(plc, nbar, driven):
     s = torch.full((m.n,) * 3, m.mu, dtype=torch.float64, device="cuda")
     c.profile_enable(timing=False)
     r = c.newton_krylov_map(dev(m.N, torch.int32), None, nbar, s=s, device_driven=driven,
+                            raise_on_fail=False)
+    assert r.status == INVALID_ARG
+    assert all(v[0] == 0 for v in c.profile_read().values())
+    assert torch.all(s == m.mu)
+
+
+@pytest.mark.parametrize("start", [-1, 3])
+def test_bad_start_option_is_refused_before_any_launch(plc, start):
+    m = small_mock(16, "uniform")
+    c = _ctx(plc, m, "mixed")
+    s = torch.full((m.n,) * 3, m.mu, dtype=torch.float64, device="cuda")
+    c.profile_enable(timing=False)
+    r = c.newton_krylov_map(dev(m.N, torch.int32), None, m.nbar, s=s, start=start,
                             raise_on_fail=False)
     assert r.status == INVALID_ARG
     assert all(v[0] == 0 for v in c.profile_read().values())

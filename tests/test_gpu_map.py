@@ -181,3 +181,44 @@ def test_map_start_point_option(plc, precision):
     assert r1.stats["grad_ffts"] == r0.stats["grad_ffts"]      # no transform for g(mu)
     bar = 1e-8 if precision == "fp64" else 1e-4
     assert np.max(np.abs(host(r0.s) - host(r1.s))) <= bar
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("driven", [0, 1])
+def test_start_at_mean_reads_no_start_array(plc, precision, driven):
+    """opts.start = 2 is opts.start = 1 with the caller's start taken to be
+    mu without reading the array: on an array full of NaN it gives the same
+    MAP, bit for bit, and the same statistics as start = 1 on an array
+    filled with mu (selection and angular mask, so w is read)."""
+    m = _mock("sel24")
+    c = plc.Context(m.n, m.box, precision)
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    Nd, wd = dev(m.N, torch.int32), dev(m.w, torch.float64)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    s1 = torch.full((m.n,) * 3, m.mu, dtype=torch.float64, device="cuda")
+    s2 = torch.full((m.n,) * 3, float("nan"), dtype=torch.float64, device="cuda")
+    r1 = c.newton_krylov_map(Nd, wd, m.nbar, s=s1, tol=tol, start=1, device_driven=driven)
+    r2 = c.newton_krylov_map(Nd, wd, m.nbar, s=s2, tol=tol, start=2, device_driven=driven)
+    assert torch.equal(s1, s2)
+    for k in ("newton_iters", "cg_iters", "grad_evals", "grad_ffts", "grad_ffts_fp64",
+              "g0_norm", "grad_rel", "neg_logpost"):
+        assert r1.stats[k] == r2.stats[k], k
+    if driven:
+        # the same kernels less the control kernel of the never-taken IF node
+        # that start = 1 keeps for a start off the mean
+        assert r2.stats["kernels"] == r1.stats["kernels"] - 1
+
+
+def test_gauss_map_start_at_zero_reads_no_start_array(plc):
+    """The same option for the Gaussian-prior model: delta taken to be 0."""
+    m = _mock("sel24")
+    c = plc.Context(m.n, m.box, "fp64")
+    c.set_prior(m.k_tab, m.P_tab, m.mu)
+    Nd, wd = dev(m.N, torch.int32), dev(m.w, torch.float64)
+    d1 = torch.zeros((m.n,) * 3, dtype=torch.float64, device="cuda")
+    d2 = torch.full((m.n,) * 3, float("nan"), dtype=torch.float64, device="cuda")
+    r1 = c.gauss_map(Nd, wd, m.nbar, delta=d1, tol=1e-10, start=1)
+    r2 = c.gauss_map(Nd, wd, m.nbar, delta=d2, tol=1e-10, start=2)
+    assert torch.equal(d1, d2)
+    for k in ("newton_iters", "cg_iters", "grad_evals", "g0_norm", "grad_rel"):
+        assert r1.stats[k] == r2.stats[k], k
