@@ -141,6 +141,29 @@ def test_batch_equals_one_by_one(plc):
         assert torch.equal(r.s, s)
 
 
+def test_batch_start_at_mean_reads_no_start_arrays(plc):
+    """opts.start = 2 in a batch: start arrays full of NaN give the same MAPs,
+    bit for bit, and the same iterations as start = 1 from arrays filled
+    with mu."""
+    ms = [small_mock(32, "uniform", sigma=1.0, nbar=2.0, seed=3),
+          small_mock(48, "radial_masked", sigma=1.3, nbar=0.7, seed=4),
+          small_mock(24, "radial_masked", sigma=0.9, nbar=1.5, seed=6)]
+    cs = [_ctx(plc, m, p) for m, p in zip(ms, ["mixed", "fp64", "mixed"])]
+    Ns = [dev(m.N, torch.int32) for m in ms]
+    ws = [dev(m.w, torch.float64) for m in ms]
+    nb = [m.nbar for m in ms]
+    s1 = [torch.full((m.n,) * 3, m.mu, dtype=torch.float64, device="cuda") for m in ms]
+    s2 = [torch.full((m.n,) * 3, float("nan"), dtype=torch.float64, device="cuda") for m in ms]
+    b = plc.Batch(cs)
+    st1, stats1 = b.map(Ns, ws, nb, s1, tol=1e-8, start=1)
+    st2, stats2 = b.map(Ns, ws, nb, s2, tol=1e-8, start=2)   # captured again: new key
+    assert st1 == 0 and st2 == 0
+    for a, c, x, y in zip(s1, s2, stats1, stats2):
+        assert torch.equal(a, c)
+        for k in ITER_KEYS:
+            assert x[k] == y[k], k
+
+
 @pytest.mark.parametrize("tol", [4e-7, 3e-7, 2e-7, 1.5e-7, 1e-7])
 def test_drivers_agree_near_the_fp32_floor(plc, tol):
     """Mixed solves whose tolerance sits near the FP32 gradient's rounding
